@@ -1,0 +1,69 @@
+"""Plant plausible mistakes in a copy of the oracle (on the CPU) and check
+that the pins of test_oracle.py catch each one: a dropped term, a wrong
+sign convention, a wrong index and a wrong tau formula."""
+import ctypes
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from tests import test_oracle as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "qr_oracle.c")
+
+MUTANTS = {
+    "dropped_pivot_term": ("      double w = a[0];\n      for (int64_t r = 0; r < len; ++r) w += v[r] * a[r + 1];\n      w *= t;\n      a[0] -= w;\n      for (int64_t r = 0; r < len; ++r) a[r + 1] -= w * v[r];\n    }\n  }\n  return 0;\n}\n\n/* C <- Q^T C",
+                           "      double w = 0.0;\n      for (int64_t r = 0; r < len; ++r) w += v[r] * a[r + 1];\n      w *= t;\n      a[0] -= w;\n      for (int64_t r = 0; r < len; ++r) a[r + 1] -= w * v[r];\n    }\n  }\n  return 0;\n}\n\n/* C <- Q^T C"),
+    "flipped_beta_sign": ("double beta = (a < 0.0) ? norm : -norm;", "double beta = (a < 0.0) ? -norm : norm;"),
+    "shifted_row_index": ("      a[0] -= w;\n      for (int64_t r = 0; r < len; ++r) a[r + 1] -= w * v[r];\n    }\n  }\n  return 0;\n}\n\n/* C <- Q^T C",
+                          "      a[0] -= w;\n      for (int64_t r = 0; r < len; ++r) a[r] -= w * v[r];\n    }\n  }\n  return 0;\n}\n\n/* C <- Q^T C"),
+    "wrong_tau": ("double tau = (beta - a) / beta;", "double tau = (beta - a) / a;"),
+}
+
+PIN_TESTS = [
+    lambda: pins.test_closed_form_2x2(),
+    lambda: pins.test_constructed_q0_r0(0),
+    lambda: pins.test_rtr_equals_ata(),
+    lambda: pins.test_against_long_double_mgs(8, 5),
+    lambda: pins.test_backward_and_orthogonality(128, 128),
+]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor not found: " + name
+    tmp = tempfile.mkdtemp()
+    try:
+        c = os.path.join(tmp, "m.c")
+        so = os.path.join(tmp, "libm.so")
+        open(c, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, c, "-lm"])
+        saved = oracle._lib
+        oracle._lib = None
+        oracle.lib()  # sets argtypes on the real library
+        real = oracle._lib
+        mut = ctypes.CDLL(so)
+        # copy signatures onto the mutant
+        for sym in ["oracle_geqr2", "oracle_apply_qt", "oracle_apply_q", "oracle_form_q", "oracle_trsm_upper",
+                    "oracle_mgs_ld", "oracle_fact_residual", "oracle_orth_residual", "oracle_ls_solve",
+                    "oracle_ls_refine", "oracle_set_threads"]:
+            getattr(mut, sym).argtypes = getattr(real, sym).argtypes
+            getattr(mut, sym).restype = getattr(real, sym).restype
+        oracle._lib = mut
+        caught = 0
+        try:
+            for t in PIN_TESTS:
+                try:
+                    t()
+                except AssertionError:
+                    caught += 1
+        finally:
+            oracle._lib = saved
+        assert caught >= 1, "no pin caught mutant " + name
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
