@@ -1,0 +1,155 @@
+"""GB300-native tile Householder QR with an empirical NB/IB autotuner.
+
+The method is Agullo, Dongarra, Nath, Tomov, "A Fully Empirical Autotuned
+Dense QR Factorization for Multicore Architectures" (tile QR, Sec. 2; the
+empirical tuner, Secs. 4-5), re-designed for one GB300 GPU. The compute
+path lives in the CUDA library ``libtileqr.so`` behind the C ABI of
+``include/tileqr.h``; this package is its Python binding. PyTorch is used
+only for device memory and streams.
+
+Matrices are column-major: a torch tensor ``A`` of shape (m, n) with
+``A.stride() == (1, lda)`` (see :func:`colmajor`).
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+
+QR_PREC_F64 = 0
+QR_PREC_F32 = 1
+QR_DEV_TIMEOUT = 1
+QR_DEV_NONFINITE = 2
+QR_OPT_WAIT_TIMEOUT_US = 1
+QR_OPT_CTAS_PER_SM = 2
+QR_OPT_SPLIT = 3
+QR_OPT_GRID_LIMIT = 4
+QR_OPT_DROP_TASK = 5
+
+
+def lib():
+    return _lib.load()
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def colmajor(x):
+    """Column-major copy (or view, when already column-major) of a 2-D tensor."""
+    if x.dim() == 1:
+        x = x[:, None]
+    if x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def colmajor_empty(m, n, dtype, device="cuda"):
+    return torch.empty((n, m), dtype=dtype, device=device).t()
+
+
+def _prec(dtype):
+    if dtype == torch.float64:
+        return QR_PREC_F64
+    if dtype == torch.float32:
+        return QR_PREC_F32
+    raise TypeError("dtype must be float64 or float32")
+
+
+def qr_workspace(m, n, nb, ib, dtype=torch.float64):
+    """(t_elems, scratch_bytes) for qr_factor."""
+    t = ctypes.c_int64()
+    s = ctypes.c_int64()
+    _lib.check(lib().qr_workspace(m, n, nb, ib, _prec(dtype), ctypes.byref(t), ctypes.byref(s)), "qr_workspace")
+    return t.value, s.value
+
+
+class Factorization:
+    """Result of qr_factor: A overwritten with R and the tile reflectors, the
+    T factors, and the scratch buffer (which holds the device status word)."""
+
+    def __init__(self, A, T, scratch, nb, ib):
+        self.A, self.T, self.scratch, self.nb, self.ib = A, T, scratch, nb, ib
+        self.m, self.n = A.shape
+
+    def R(self):
+        return torch.triu(self.A[: self.n, :])
+
+    def status(self, stream=None):
+        return qr_status(self.scratch, stream)
+
+
+def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None):
+    """Tile QR of A (in place). ``nb = 0`` uses the tuned table."""
+    m, n = A.shape
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if A.stride(0) != 1:
+        raise ValueError("A must be column-major (use colmajor())")
+    lda = A.stride(1) if n > 1 else m
+    if nb == 0:
+        nb, ib = qr_lookup(m, n, A.dtype)
+    t_elems, sbytes = qr_workspace(m, n, nb, ib, A.dtype)
+    if T is None or T.numel() < t_elems:
+        T = torch.empty(max(t_elems, 1), dtype=A.dtype, device=A.device)
+    if scratch is None or scratch.numel() < sbytes:
+        scratch = torch.empty(sbytes, dtype=torch.uint8, device=A.device)
+    f = lib().qr_factor_d if A.dtype == torch.float64 else lib().qr_factor_s
+    _lib.check(f(m, n, ctypes.c_void_p(A.data_ptr()), lda, nb, ib, ctypes.c_void_p(T.data_ptr()),
+                 ctypes.c_void_p(scratch.data_ptr()), sbytes, _stream_ptr(stream)), "qr_factor")
+    return Factorization(A, T, scratch, nb, ib)
+
+
+def qr_apply_qt(fact, C, trans=True, stream=None):
+    """C <- Q^T C (trans) or Q C, in place, with the factors of qr_factor."""
+    if C.stride(0) != 1:
+        raise ValueError("C must be column-major (use colmajor())")
+    if C.dtype != fact.A.dtype:
+        raise TypeError("C must have the factorization's dtype")
+    m, n = fact.m, fact.n
+    nrhs = C.shape[1]
+    ldc = C.stride(1) if nrhs > 1 else m
+    f = lib().qr_apply_qt_d if C.dtype == torch.float64 else lib().qr_apply_qt_s
+    lda = fact.A.stride(1) if n > 1 else m
+    _lib.check(f(m, n, nrhs, ctypes.c_void_p(fact.A.data_ptr()), lda, fact.nb, fact.ib,
+                 ctypes.c_void_p(fact.T.data_ptr()), ctypes.c_void_p(C.data_ptr()), ldc, 1 if trans else 0,
+                 _stream_ptr(stream)), "qr_apply_qt")
+    return C
+
+
+def form_q(fact, stream=None):
+    """Explicit thin Q (m x n) = Q [I; 0], on the GPU."""
+    Q = colmajor_empty(fact.m, fact.n, fact.A.dtype, fact.A.device)
+    Q.zero_()
+    Q.diagonal().fill_(1)
+    return qr_apply_qt(fact, Q, trans=False, stream=stream)
+
+
+def qr_status(scratch, stream=None):
+    st = ctypes.c_int()
+    _lib.check(lib().qr_status(ctypes.c_void_p(scratch.data_ptr()), ctypes.byref(st), _stream_ptr(stream)),
+               "qr_status")
+    return st.value
+
+
+def qr_set_option(opt, value):
+    _lib.check(lib().qr_set_option(opt, int(value)), "qr_set_option")
+
+
+def qr_get_option(opt):
+    return lib().qr_get_option(opt)
+
+
+def qr_task_count(m, n, nb, ib):
+    return lib().qr_task_count(m, n, nb, ib)
+
+
+def qr_lookup(m, n, dtype=torch.float64):
+    """(nb, ib) from the loaded tuning table (built-in default otherwise)."""
+    return 128, 32
+
+
+def qr_flops(m, n):
+    """Credited flops 2mn^2 - 2n^3/3 (= 4/3 N^3 when m = n, Sec. 2.2)."""
+    return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0

@@ -1,0 +1,57 @@
+"""ctypes binding of libtileqr.so: the C ABI of include/tileqr.h with the
+same names, argument marshalling only. Every computation runs in the CUDA
+library; there is no Python or CPU fallback: if the library cannot be built
+or loaded, loading raises."""
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+c_i64 = ctypes.c_int64
+c_int = ctypes.c_int
+c_vp = ctypes.c_void_p
+c_dbl = ctypes.c_double
+
+# (name, restype, argtypes) for every symbol of include/tileqr.h
+SIGNATURES = [
+    ("qr_workspace", c_int, [c_i64, c_i64, c_int, c_int, c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    ("qr_factor_d", c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_vp]),
+    ("qr_factor_s", c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_vp]),
+    ("qr_apply_qt_d", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp]),
+    ("qr_apply_qt_s", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp]),
+    ("qr_status", c_int, [c_vp, ctypes.POINTER(c_int), c_vp]),
+    ("qr_set_option", c_int, [c_int, c_i64]),
+    ("qr_get_option", c_i64, [c_int]),
+    ("qr_task_count", c_i64, [c_i64, c_i64, c_int, c_int]),
+]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load (building first if needed) libtileqr.so and set its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libtileqr.so is not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(rc, what):
+    if rc != 0:
+        raise RuntimeError("%s failed with code %d" % (what, rc))
+    return rc

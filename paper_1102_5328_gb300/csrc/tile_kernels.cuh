@@ -1,0 +1,497 @@
+// Device building blocks of the tile Householder QR (flat tree).
+//
+// The four tile kernels the paper builds its QR from (Sec. 2.1): GEQRT (QR of
+// a diagonal tile), TSQRT (QR of a triangle stacked on a square tile), UNMQR
+// (the paper's DLARFB: apply GEQRT's Q^T to a tile to its right) and TSMQR
+// (the paper's DSSRFB: apply TSQRT's Q^T to a pair of tiles). Inner blocking
+// IB (Sec. 2.2) groups the reflectors of a tile into blocks of IB whose
+// product is I - V T V^T with T upper triangular (compact WY form).
+//
+// Execution model: one CTA of NTHREADS threads runs one task. FP64 on this
+// GPU issues roughly 2 fused multiply-adds per clock per SM, so every kernel
+// is bound by the FP64 pipe, not by memory: the code spends shared memory and
+// registers freely to keep that pipe fed and to avoid non-FMA FP64 work.
+//
+// Memory discipline inside the persistent scheduler: any tile another CTA may
+// have written is read with ld.global.cg (L2, bypassing the non-coherent L1)
+// and written with st.global.cg, so no SM ever consumes a stale L1 line.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tileqr.h"
+
+namespace tqr {
+
+constexpr int NTHREADS = 256;
+constexpr int RPT = 32;          // rows of C held in registers per thread (apply)
+constexpr int VS_CAP = 4096;     // elements of the staged V panel
+constexpr int PG = 8;            // reflectors per partial-sum group (apply)
+constexpr int PART_CAP = PG * NTHREADS;
+constexpr int W_CAP = 4096;      // elements of W = T^T V^T C for one chunk
+constexpr int PANEL_CAP = PART_CAP + W_CAP;  // level-2 sub-panel (aliases part + W): 6144
+constexpr int TS_CAP = 1024;     // sub-block T (<= 32 x 32)
+constexpr int RED_CAP = 64;
+
+// Shared-memory carve-up (in elements of S) used by every task.
+template <typename S>
+struct Smem {
+  S* vs;     // [VS_CAP]
+  S* part;   // [PART_CAP]
+  S* w;      // [W_CAP]
+  S* ts;     // [TS_CAP]
+  S* red;    // [RED_CAP]
+  S* tau;    // [512]
+  S* rs;     // [TS_CAP] R sub-block (TSQRT level-2)
+};
+
+template <typename S>
+__host__ __device__ constexpr size_t smem_elems() {
+  return (size_t)VS_CAP + PART_CAP + W_CAP + TS_CAP + RED_CAP + 512 + TS_CAP;
+}
+
+template <typename S>
+__device__ __forceinline__ Smem<S> carve(S* base) {
+  Smem<S> s;
+  s.vs = base;
+  s.part = s.vs + VS_CAP;
+  s.w = s.part + PART_CAP;
+  s.ts = s.w + W_CAP;
+  s.red = s.ts + TS_CAP;
+  s.tau = s.red + RED_CAP;
+  s.rs = s.tau + 512;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// coherent (L2) global access helpers
+template <typename S>
+__device__ __forceinline__ S ldg(const S* p) { return __ldcg(p); }
+template <typename S>
+__device__ __forceinline__ void stg(S* p, S v) { __stcg(p, v); }
+// a pointer that may be shared (generic) or global (L2-coherent path)
+template <typename S>
+__device__ __forceinline__ S ldx(const S* p, bool sm) { return sm ? *p : __ldcg(p); }
+template <typename S>
+__device__ __forceinline__ void stx(S* p, S v, bool sm) {
+  if (sm) *p = v; else __stcg(p, v);
+}
+
+template <typename S>
+__device__ __forceinline__ S warp_sum(S v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// CTA-wide sum; every thread gets the result. Uses red[0..NTHREADS/32].
+template <typename S>
+__device__ __forceinline__ S cta_sum(S v, S* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  S t = (threadIdx.x < NTHREADS / 32) ? red[threadIdx.x] : S(0);
+  if (wid == 0) {
+    t = warp_sum(t);
+    if (lane == 0) red[NTHREADS / 32] = t;
+  }
+  __syncthreads();
+  return red[NTHREADS / 32];
+}
+
+// ---------------------------------------------------------------------------
+// Apply Q_l^T of blocks of reflectors to a range of columns.
+//
+// GE mode (UNMQR; trailing update inside GEQRT): reflector p of a block that
+// starts at row/column l0 is v_p = [0 (rows < l0+p); 1; V(l0+p+1:rows, l0+p)]
+// from the tile V; C is one tile whose rows [0, rows) all live in registers.
+// TS mode (TSMQR; trailing update inside TSQRT): reflector p is
+// [e_{l0+p} (top tile); V(0:rows, l0+p) (bottom tile)], Ctop is the top tile
+// and C the bottom tile.
+// For each block of ib reflectors: W = Vfull^T Cstack, W <- T_l^T W,
+// Cstack -= Vfull W, with T_l the upper-triangular ib x ib factor stored at
+// T + l0*ldt (element (q, p) at T[q + (l0+p)*ldt]).
+// Blocks run from l0 = lstart to lend in steps of IB.
+//
+// Thread layout: C's column chunk of width cw is split in G = ceil(rows/RPT)
+// row groups; thread (g, c) keeps C(g*RPT : g*RPT+RPT, c) in registers for
+// all blocks, so C is read and written once per task.
+//
+// TR = true applies Q^T (blocks in ascending order, W <- T^T W); TR = false
+// applies Q (blocks in descending order, W <- T W).
+template <typename S, bool TS, bool TR = true>
+__device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, bool t_smem,
+                         int lstart, int lend, int IB, S* Ctop, int ldct, S* C, int ldc, int rows,
+                         int c0, int c1, const Smem<S>& sm) {
+  if (c1 <= c0 || lend <= lstart || rows <= 0) return;
+  const int tid = threadIdx.x;
+  const int G = (rows + RPT - 1) / RPT;
+  const int ibmax = min(IB, lend - lstart);
+  const int cwmax = min(NTHREADS / G, W_CAP / ibmax);
+  const int nchunks = (c1 - c0 + cwmax - 1) / cwmax;
+  const int per = (c1 - c0 + nchunks - 1) / nchunks;
+  for (int cs = c0; cs < c1; cs += per) {
+    const int cw = min(per, c1 - cs);
+    const int g = tid / cw, c = tid - (tid / cw) * cw;
+    const bool act = g < G;
+    S creg[RPT];
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int r = g * RPT + rr;
+      creg[rr] = (act && r < rows) ? ldg(C + r + (size_t)(cs + c) * ldc) : S(0);
+    }
+    const int nblk = (lend - lstart + IB - 1) / IB;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int l0 = lstart + (TR ? bi : nblk - 1 - bi) * IB;
+      const int ib = min(IB, lend - l0);
+      // rows below rlo_al are untouched by this block (GE); whole groups skip
+      const int rlo = TS ? 0 : l0;
+      const int glo = rlo / RPT;
+      const int rlo_al = glo * RPT;
+      const int nr = G * RPT - rlo_al;  // staged rows, zero-padded past `rows`
+      int PB = VS_CAP / nr;
+      if (PB > ib) PB = ib;
+      if (PB < 1) PB = 1;
+      const bool myrows = act && g >= glo;
+      // --- phase A: W = Vfull^T Cstack, V staged PB reflectors at a time
+      for (int pp0 = 0; pp0 < ib; pp0 += PB) {
+        const int pb = min(PB, ib - pp0);
+        __syncthreads();
+        for (int idx = tid; idx < pb * nr; idx += NTHREADS) {
+          const int p = idx / nr, rl = idx - (idx / nr) * nr;
+          const int r = rl + rlo_al, pc = l0 + pp0 + p;
+          S v = S(0);
+          if (r < rows) {
+            if (TS) {
+              v = ldg(V + r + (size_t)pc * ldv);
+            } else {
+              v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
+            }
+          }
+          sm.vs[rl * PB + p] = v;
+        }
+        __syncthreads();
+        for (int pg0 = 0; pg0 < pb; pg0 += PG) {
+          const int pgc = min(PG, pb - pg0);
+          if (myrows) {
+            S acc[PG];
+#pragma unroll
+            for (int q = 0; q < PG; ++q) acc[q] = S(0);
+            const S* vrow = sm.vs + (size_t)(g * RPT - rlo_al) * PB + pg0;
+#pragma unroll
+            for (int rr = 0; rr < RPT; ++rr) {
+              const S cv = creg[rr];
+#pragma unroll
+              for (int q = 0; q < PG; ++q)
+                if (q < pgc) acc[q] = fma(vrow[rr * PB + q], cv, acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < PG; ++q)
+              if (q < pgc) sm.part[(q * G + g) * cw + c] = acc[q];
+          }
+          __syncthreads();
+          for (int o = tid; o < pgc * cw; o += NTHREADS) {
+            const int q = o / cw, cc = o - (o / cw) * cw;
+            const int p = pp0 + pg0 + q;
+            S s = TS ? ldg(Ctop + (l0 + p) + (size_t)(cs + cc) * ldct) : S(0);
+            for (int gg = glo; gg < G; ++gg) s += sm.part[(q * G + gg) * cw + cc];
+            sm.w[p * cw + cc] = s;
+          }
+          __syncthreads();
+        }
+      }
+      // --- phase B: W <- T_l^T W; TS: Ctop rows -= W
+      {
+        S wq[16];
+        int no = 0;
+        for (int o = tid; o < ib * cw && no < 16; o += NTHREADS, ++no) {
+          const int p = o / cw, cc = o - (o / cw) * cw;
+          S s = S(0);
+          if (TR) {
+            const S* tcol = T + (size_t)(l0 + p) * ldt;
+            for (int q = 0; q <= p; ++q) s = fma(ldx(tcol + q, t_smem), sm.w[q * cw + cc], s);
+          } else {
+            const S* trow = T + p + (size_t)l0 * ldt;
+            for (int q = p; q < ib; ++q) s = fma(ldx(trow + (size_t)q * ldt, t_smem), sm.w[q * cw + cc], s);
+          }
+          wq[no] = s;
+        }
+        __syncthreads();
+        no = 0;
+        for (int o = tid; o < ib * cw && no < 16; o += NTHREADS, ++no) {
+          const int p = o / cw, cc = o - (o / cw) * cw;
+          sm.w[p * cw + cc] = wq[no];
+          if (TS) {
+            S* pt = Ctop + (l0 + p) + (size_t)(cs + cc) * ldct;
+            stg(pt, ldg(pt) - wq[no]);
+          }
+        }
+        __syncthreads();
+      }
+      // --- phase C: Cstack -= Vfull W (restage V if it did not fit at once)
+      for (int pp0 = 0; pp0 < ib; pp0 += PB) {
+        const int pb = min(PB, ib - pp0);
+        if (PB < ib) {
+          __syncthreads();
+          for (int idx = tid; idx < pb * nr; idx += NTHREADS) {
+            const int p = idx / nr, rl = idx - (idx / nr) * nr;
+            const int r = rl + rlo_al, pc = l0 + pp0 + p;
+            S v = S(0);
+            if (r < rows) {
+              if (TS) {
+                v = ldg(V + r + (size_t)pc * ldv);
+              } else {
+                v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
+              }
+            }
+            sm.vs[rl * PB + p] = v;
+          }
+          __syncthreads();
+        }
+        if (myrows) {
+          const S* vrow = sm.vs + (size_t)(g * RPT - rlo_al) * PB;
+          for (int p = 0; p < pb; ++p) {
+            const S wv = sm.w[(pp0 + p) * cw + c];
+#pragma unroll
+            for (int rr = 0; rr < RPT; ++rr) creg[rr] = fma(-vrow[rr * PB + p], wv, creg[rr]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int r = g * RPT + rr;
+      if (act && r < rows) stg(C + r + (size_t)(cs + c) * ldc, creg[rr]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// T factor of a block of ncol reflectors (LAPACK's forward, columnwise
+// recurrence): T(p,p) = tau_p, T(0:p,p) = -tau_p T(0:p,0:p) (V^T v_p)(0:p).
+// V(r, q) for r in [0, nr): GE: unit at r = q, zero above (rows relative to
+// the block's first row); TS: full column (the stacked identity part is
+// orthogonal between reflectors and drops out of V^T V).
+template <typename S, bool TS>
+__device__ void build_t(const S* V, int ldv, bool v_smem, int nr, int ncol, const S* tau, S* Tout,
+                        int ldt, bool t_smem) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // Gram entries z(q,p), q < p, into T's strict upper triangle
+  const int npairs = ncol * (ncol - 1) / 2;
+  for (int pr = wid; pr < npairs; pr += NTHREADS / 32) {
+    // decode pair index -> (q, p) with q < p (column-major over p)
+    int p = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)pr)) * 0.5f);
+    while (p * (p - 1) / 2 > pr) --p;
+    while ((p + 1) * p / 2 <= pr) ++p;
+    const int q = pr - p * (p - 1) / 2;
+    S s = S(0);
+    const int r0 = TS ? 0 : p + 1;
+    for (int r = r0 + lane; r < nr; r += 32)
+      s = fma(ldx(V + r + (size_t)q * ldv, v_smem), ldx(V + r + (size_t)p * ldv, v_smem), s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (!TS) s += ldx(V + p + (size_t)q * ldv, v_smem);
+      stx(Tout + q + (size_t)p * ldt, s, t_smem);
+    }
+  }
+  for (int p = threadIdx.x; p < ncol; p += NTHREADS) stx(Tout + p + (size_t)p * ldt, tau[p], t_smem);
+  __syncthreads();
+  for (int p = 1; p < ncol; ++p) {
+    const S tp = tau[p];
+    S t = S(0);
+    const int q = threadIdx.x;
+    if (q < p && tp != S(0)) {
+      for (int s2 = q; s2 < p; ++s2)
+        t = fma(ldx(Tout + q + (size_t)s2 * ldt, t_smem), ldx(Tout + s2 + (size_t)p * ldt, t_smem), t);
+    }
+    __syncthreads();
+    if (q < p) stx(Tout + q + (size_t)p * ldt, -tp * t, t_smem);
+    __syncthreads();
+  }
+}
+// (ncol <= NTHREADS is required by the recurrence above: IB <= 256.)
+
+// ---------------------------------------------------------------------------
+// Level-2 Householder QR of a sub-panel held in shared memory.
+// GE: P(nr x w), column jj has its pivot at row jj, x = P(jj+1:nr, jj).
+// TS: pivot R(jj, jj) in Rs (w x w, upper), x = P(0:nr, jj), the update
+//     touches Rs(jj, c) and P(:, c).
+// Writes tau[0..w) and reports a non-finite norm through *bad.
+template <typename S, bool TS>
+__device__ void panel_l2(S* P, int ldp, int nr, int w, S* Rs, int ldr, S* tau, S* red, int* bad) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int jj = 0; jj < w; ++jj) {
+    const int x0 = TS ? 0 : jj + 1;
+    S* col = P + (size_t)jj * ldp;
+    S s = S(0);
+    for (int r = x0 + threadIdx.x; r < nr; r += NTHREADS) s = fma(col[r], col[r], s);
+    const S xi2 = cta_sum(s, red);  // ends with a barrier
+    S* piv = TS ? (Rs + jj + (size_t)jj * ldr) : (col + jj);
+    if (threadIdx.x == 0) {
+      S tau_j = S(0), scal = S(0);
+      const S a = *piv;
+      if (!isfinite(xi2) || !isfinite(a)) {
+        atomicOr(bad, QR_DEV_NONFINITE);
+      } else if (xi2 != S(0)) {
+        const S nrm = sqrt(a * a + xi2);
+        const S beta = (a < S(0)) ? nrm : -nrm;
+        tau_j = (beta - a) / beta;
+        scal = S(1) / (a - beta);
+        *piv = beta;
+      }
+      tau[jj] = tau_j;
+      red[NTHREADS / 32 + 1] = scal;
+    }
+    __syncthreads();
+    const S scal = red[NTHREADS / 32 + 1];
+    const S tj = tau[jj];
+    for (int r = x0 + threadIdx.x; r < nr; r += NTHREADS) col[r] *= scal;
+    __syncthreads();
+    if (tj != S(0)) {
+      for (int cc = jj + 1 + wid; cc < w; cc += NTHREADS / 32) {
+        S* pc = P + (size_t)cc * ldp;
+        S d = S(0);
+        for (int r = x0 + lane; r < nr; r += 32) d = fma(col[r], pc[r], d);
+        d = warp_sum(d);
+        S* top = TS ? (Rs + jj + (size_t)cc * ldr) : (pc + jj);
+        const S wv = tj * (*top + d);
+        __syncwarp();
+        if (lane == 0) *top -= wv;
+        for (int r = x0 + lane; r < nr; r += 32) pc[r] = fma(-wv, col[r], pc[r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GEQRT: QR of the diagonal tile A (rows x cols, ld lda, rows >= cols),
+// T (IB x cols, ld IB). Inner blocks of IB; each block is factored in
+// sub-panels that fit shared memory (a sub-panel is applied to the rest of
+// its block with its own temporary T), then T_l is formed and the block is
+// applied to the tile's trailing columns.
+template <typename S>
+__device__ void geqrt(S* A, int lda, int rows, int cols, int IB, S* T, const Smem<S>& sm, int* bad) {
+  for (int l0 = 0; l0 < cols; l0 += IB) {
+    const int ib = min(IB, cols - l0);
+    const int nrb = rows - l0;  // rows of the block from its first row
+    int sb = PANEL_CAP / nrb;
+    if (sb > ib) sb = ib;
+    if (sb > 32 && sb < ib) sb = 32;
+    for (int s0 = l0; s0 < l0 + ib; s0 += sb) {
+      const int w = min(sb, l0 + ib - s0);
+      const int nr = rows - s0;
+      S* P = sm.part;  // nr x w, ld nr
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nr * w; idx += NTHREADS) {
+        const int cc = idx / nr, r = idx - cc * nr;
+        P[idx] = ldg(A + (s0 + r) + (size_t)(s0 + cc) * lda);
+      }
+      __syncthreads();
+      panel_l2<S, false>(P, nr, nr, w, nullptr, 0, sm.tau + (s0 - l0), sm.red, bad);
+      const bool whole = (w == ib);
+      if (whole) {
+        build_t<S, false>(P, nr, true, nr, w, sm.tau, T + (size_t)l0 * IB, IB, false);
+      } else if (s0 + w < l0 + ib) {
+        build_t<S, false>(P, nr, true, nr, w, sm.tau + (s0 - l0), sm.ts, w, true);
+      }
+      for (int idx = threadIdx.x; idx < nr * w; idx += NTHREADS) {
+        const int cc = idx / nr, r = idx - cc * nr;
+        stg(A + (s0 + r) + (size_t)(s0 + cc) * lda, P[idx]);
+      }
+      __syncthreads();
+      if (!whole && s0 + w < l0 + ib) {
+        // apply the sub-panel to the rest of the block (columns s0+w .. l0+ib)
+        apply_qt<S, false>(A, lda, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, nullptr, 0, A, lda,
+                           rows, s0 + w, l0 + ib, sm);
+      }
+    }
+    if (sb < ib) {
+      __syncthreads();
+      build_t<S, false>(A + l0 + (size_t)l0 * lda, lda, false, nrb, ib, sm.tau, T + (size_t)l0 * IB, IB,
+                        false);
+    }
+    __syncthreads();
+    if (l0 + ib < cols)
+      apply_qt<S, false>(A, lda, T, IB, false, l0, l0 + ib, IB, nullptr, 0, A, lda, rows, l0 + ib, cols, sm);
+    __syncthreads();
+  }
+}
+
+// TSQRT: QR of [R (upper triangle of the diagonal tile, ldr); B (rows x
+// cols, ldb)]. B receives the reflectors' lower parts, R the new triangle,
+// T (IB x cols) the block factors. Never touches R's strict lower part.
+template <typename S>
+__device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, S* T, const Smem<S>& sm,
+                      int* bad) {
+  for (int l0 = 0; l0 < cols; l0 += IB) {
+    const int ib = min(IB, cols - l0);
+    int sb = PANEL_CAP / rows;
+    if (sb > ib) sb = ib;
+    if (sb > 32) sb = 32;  // the R sub-block lives in rs (<= 32 x 32)
+    for (int s0 = l0; s0 < l0 + ib; s0 += sb) {
+      const int w = min(sb, l0 + ib - s0);
+      S* P = sm.part;  // rows x w
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < rows * w; idx += NTHREADS) {
+        const int cc = idx / rows, r = idx - cc * rows;
+        P[idx] = ldg(B + r + (size_t)(s0 + cc) * ldb);
+      }
+      for (int idx = threadIdx.x; idx < w * w; idx += NTHREADS) {
+        const int cc = idx / w, r = idx - cc * w;
+        sm.rs[idx] = (r <= cc) ? ldg(R + (s0 + r) + (size_t)(s0 + cc) * ldr) : S(0);
+      }
+      __syncthreads();
+      panel_l2<S, true>(P, rows, rows, w, sm.rs, w, sm.tau + (s0 - l0), sm.red, bad);
+      const bool whole = (w == ib);
+      if (whole) {
+        build_t<S, true>(P, rows, true, rows, w, sm.tau, T + (size_t)l0 * IB, IB, false);
+      } else if (s0 + w < l0 + ib) {
+        build_t<S, true>(P, rows, true, rows, w, sm.tau + (s0 - l0), sm.ts, w, true);
+      }
+      for (int idx = threadIdx.x; idx < rows * w; idx += NTHREADS) {
+        const int cc = idx / rows, r = idx - cc * rows;
+        stg(B + r + (size_t)(s0 + cc) * ldb, P[idx]);
+      }
+      for (int idx = threadIdx.x; idx < w * w; idx += NTHREADS) {
+        const int cc = idx / w, r = idx - cc * w;
+        if (r <= cc) stg(R + (s0 + r) + (size_t)(s0 + cc) * ldr, sm.rs[idx]);
+      }
+      __syncthreads();
+      if (!whole && s0 + w < l0 + ib) {
+        apply_qt<S, true>(B, ldb, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, R, ldr, B, ldb, rows,
+                          s0 + w, l0 + ib, sm);
+      }
+    }
+    if (sb < ib) {
+      __syncthreads();
+      build_t<S, true>(B + (size_t)l0 * ldb, ldb, false, rows, ib, sm.tau, T + (size_t)l0 * IB, IB, false);
+    }
+    __syncthreads();
+    if (l0 + ib < cols)
+      apply_qt<S, true>(B, ldb, T, IB, false, l0, l0 + ib, IB, R, ldr, B, ldb, rows, l0 + ib, cols, sm);
+    __syncthreads();
+  }
+}
+
+// UNMQR: C <- Q^T C for the GEQRT factors (V in the diagonal tile, rows x
+// nref reflectors, T IB x nref), columns [c0, c1) of C.
+template <typename S>
+__device__ void unmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C, int ldc, int c0,
+                      int c1, const Smem<S>& sm) {
+  apply_qt<S, false>(V, ldv, T, IB, false, 0, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm);
+}
+
+// TSMQR: [C1; C2] <- Q^T [C1; C2] for the TSQRT factors (V rows x nref in
+// the bottom tile, T IB x nref); C1 the top tile, C2 (rows) the bottom one.
+template <typename S>
+__device__ void tsmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C1, int ldc1, S* C2,
+                      int ldc2, int c0, int c1, const Smem<S>& sm) {
+  apply_qt<S, true>(V, ldv, T, IB, false, 0, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm);
+}
+
+}  // namespace tqr

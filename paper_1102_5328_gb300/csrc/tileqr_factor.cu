@@ -1,0 +1,505 @@
+// Tile QR factorization: layout conversion, the persistent DAG scheduler and
+// the C-ABI entry points qr_workspace / qr_factor_{d,s} / qr_status.
+//
+// Sec. 2.1 of the paper: the matrix is cut into tiles of order NB and QR is
+// a DAG of GEQRT, TSQRT, UNMQR and TSMQR tasks. Its multicore runtime
+// schedules the DAG statically over cores; here one persistent kernel keeps
+// every SM resident and hands out tasks through a global ticket counter in a
+// topological order computed on the host (earliest-start-time order of the
+// DAG, which pulls panel tasks of later steps forward - a look-ahead). A task
+// waits on per-tile progress counters (acquire loads with a time limit), runs
+// on its CTA, and publishes its tiles with a release increment.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "tile_kernels.cuh"
+#include "tileqr_internal.h"
+
+using namespace tqr;
+
+namespace {
+
+std::mutex g_mu;
+int64_t g_wait_timeout_us = 20LL * 1000 * 1000;
+int g_ctas_per_sm = 0;
+int g_split = 0;
+int g_grid_limit = 0;
+int64_t g_drop_task = -1;
+
+struct Layout {
+  int64_t m, n;
+  int NB, IB, MT, NT, S;
+  int64_t ntasks;
+  size_t off_cnt, off_tasks, off_tiles, bytes;
+  int64_t t_elems;
+};
+
+int auto_split(int NB) {
+  if (g_split > 0) return g_split;
+  if (NB <= 160) return 1;
+  if (NB <= 320) return 2;
+  return 4;
+}
+
+int64_t count_tasks(int MT, int NT, int S) {
+  int64_t c = 0;
+  const int K = std::min(MT, NT);
+  for (int k = 0; k < K; ++k) {
+    c += 1 + (int64_t)(NT - k - 1) * S;
+    c += (int64_t)(MT - k - 1) * (1 + (int64_t)(NT - k - 1) * S);
+  }
+  return c;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout make_layout(int64_t m, int64_t n, int nb, int ib, size_t esz) {
+  Layout L;
+  L.m = m; L.n = n; L.NB = nb; L.IB = ib;
+  L.MT = (int)((m + nb - 1) / nb);
+  L.NT = (int)((n + nb - 1) / nb);
+  L.S = std::min(auto_split(nb), nb);
+  L.ntasks = count_tasks(L.MT, L.NT, L.S);
+  size_t off = 256;  // status words
+  L.off_cnt = off;
+  off = align256(off + (size_t)L.MT * L.NT * L.S * sizeof(unsigned));
+  L.off_tasks = off;
+  off = align256(off + (size_t)L.ntasks * sizeof(uint64_t));
+  L.off_tiles = off;
+  off = align256(off + (size_t)L.MT * L.NT * nb * nb * esz);
+  L.bytes = off;
+  L.t_elems = (int64_t)L.MT * L.NT * ib * nb;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Host: the task order. Program order first (k-major flat tree), then the
+// earliest start time of every task in an unbounded-processor schedule with
+// flop weights, then a stable sort on it. Dependencies always start strictly
+// earlier, so the result is a topological order.
+struct SchedKey {
+  int MT, NT, S;
+  bool operator<(const SchedKey& o) const { return std::tie(MT, NT, S) < std::tie(o.MT, o.NT, o.S); }
+};
+struct Sched {
+  uint64_t* host = nullptr;  // pinned
+  int64_t n = 0;
+};
+std::map<SchedKey, Sched> g_sched;
+
+const Sched& get_schedule(int MT, int NT, int S) {
+  SchedKey key{MT, NT, S};
+  auto it = g_sched.find(key);
+  if (it != g_sched.end()) return it->second;
+  const int K = std::min(MT, NT);
+  std::vector<uint64_t> code;
+  std::vector<double> est;
+  code.reserve(count_tasks(MT, NT, S));
+  est.reserve(code.capacity());
+  std::vector<double> fin((size_t)MT * NT * S, 0.0);
+  auto F = [&](int i, int j, int s) -> double& { return fin[((size_t)j * MT + i) * S + s]; };
+  // relative costs (units of NB^3 flops); panel tasks run a latency-bound
+  // level-2 part, so they are weighted up a little
+  const double wG = 4.0 / 3.0 * 1.5, wT = 2.0 * 1.5, wU = 2.0 / S, wM = 4.0 / S;
+  for (int k = 0; k < K; ++k) {
+    {
+      double st = 0;
+      for (int s = 0; s < S; ++s) st = std::max(st, F(k, k, s));
+      for (int s = 0; s < S; ++s) F(k, k, s) = st + wG;
+      code.push_back(encode_task(TASK_GEQRT, 0, k, k, k));
+      est.push_back(st);
+    }
+    const double fin_geqrt = F(k, k, 0);
+    for (int j = k + 1; j < NT; ++j)
+      for (int s = 0; s < S; ++s) {
+        double st = std::max(fin_geqrt, F(k, j, s));
+        F(k, j, s) = st + wU;
+        code.push_back(encode_task(TASK_UNMQR, s, k, j, k));
+        est.push_back(st);
+      }
+    for (int i = k + 1; i < MT; ++i) {
+      double st = 0;
+      for (int s = 0; s < S; ++s) st = std::max(st, std::max(F(k, k, s), F(i, k, s)));
+      for (int s = 0; s < S; ++s) F(k, k, s) = F(i, k, s) = st + wT;
+      code.push_back(encode_task(TASK_TSQRT, 0, i, k, k));
+      est.push_back(st);
+      const double fin_v = st + wT;
+      for (int j = k + 1; j < NT; ++j)
+        for (int s = 0; s < S; ++s) {
+          double st2 = std::max(fin_v, std::max(F(k, j, s), F(i, j, s)));
+          F(k, j, s) = F(i, j, s) = st2 + wM;
+          code.push_back(encode_task(TASK_TSMQR, s, i, j, k));
+          est.push_back(st2);
+        }
+    }
+  }
+  std::vector<int64_t> idx(code.size());
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return est[a] < est[b]; });
+  Sched sc;
+  sc.n = (int64_t)code.size();
+  if (cudaHostAlloc((void**)&sc.host, sizeof(uint64_t) * std::max<int64_t>(sc.n, 1), cudaHostAllocDefault) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    sc.host = (uint64_t*)malloc(sizeof(uint64_t) * std::max<int64_t>(sc.n, 1));
+  }
+  for (int64_t t = 0; t < sc.n; ++t) sc.host[t] = code[idx[t]];
+  return g_sched.emplace(key, sc).first->second;
+}
+
+// ---------------------------------------------------------------------------
+// Device: layout conversion and status reset.
+template <typename S>
+__global__ void cm_to_tiles(const S* __restrict__ A, int64_t lda, int64_t m, int64_t n, S* __restrict__ W,
+                            int NB, int MT, int NT, unsigned* zero_words, int64_t nzero) {
+  const int64_t tile_elems = (int64_t)NB * NB;
+  const int64_t total = tile_elems * MT * NT;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t t = e / tile_elems;
+    const int64_t w = e - t * tile_elems;
+    const int c = (int)(w / NB), r = (int)(w - (int64_t)c * NB);
+    const int j = (int)(t / MT), i = (int)(t - (int64_t)j * MT);
+    const int64_t row = (int64_t)i * NB + r, col = (int64_t)j * NB + c;
+    W[e] = (row < m && col < n) ? A[row + col * lda] : S(0);
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nzero; e += stride) zero_words[e] = 0u;
+}
+
+template <typename S>
+__global__ void tiles_to_cm(const S* __restrict__ W, S* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                            int NB, int MT) {
+  const int64_t total = m * n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t col = e / m, row = e - col * m;
+    const int i = (int)(row / NB), j = (int)(col / NB);
+    const int r = (int)(row - (int64_t)i * NB), c = (int)(col - (int64_t)j * NB);
+    A[row + col * lda] = W[((int64_t)j * MT + i) * NB * NB + r + (int64_t)c * NB];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Device: the persistent scheduler.
+struct DevCtl {
+  int status;
+  int abort;
+  unsigned ticket;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait until all counters c[0..cnt) reach v. Bounded by time and by
+// iterations; on expiry sets the timeout bit and the abort flag.
+__device__ bool wait_ge(const unsigned* c, int cnt, unsigned v, DevCtl* ctl, uint64_t timeout_ns) {
+  const uint64_t t0 = globaltimer();
+  const uint64_t max_iter = timeout_ns / 16 + 4096;
+  uint64_t iter = 0;
+  for (int q = 0; q < cnt; ++q) {
+    while (ld_acquire(c + q) < v) {
+      if (((volatile int*)&ctl->abort)[0]) return false;
+      if (++iter > max_iter || globaltimer() - t0 > timeout_ns) {
+        atomicOr(&ctl->status, QR_DEV_TIMEOUT);
+        atomicExch(&ctl->abort, 1);
+        return false;
+      }
+      __nanosleep(100);
+    }
+  }
+  return true;
+}
+
+template <typename S>
+struct FactorArgs {
+  S* W;
+  S* T;
+  int64_t m, n;
+  int NB, IB, MT, NT, S_;
+  const uint64_t* tasks;
+  int64_t ntasks;
+  unsigned* cnt;
+  DevCtl* ctl;
+  uint64_t timeout_ns;
+};
+
+template <typename S>
+__global__ void __launch_bounds__(NTHREADS, 2) persistent_qr(FactorArgs<S> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<S> sm = carve<S>(reinterpret_cast<S*>(smem_raw));
+  __shared__ int64_t s_ticket;
+  __shared__ int s_ok;
+  const int NB = a.NB, MT = a.MT, Sp = a.S_;
+  const size_t tile_elems = (size_t)NB * NB;
+  auto tile = [&](int i, int j) { return a.W + ((size_t)j * MT + i) * tile_elems; };
+  auto tfac = [&](int i, int k) { return a.T + ((size_t)k * MT + i) * (size_t)a.IB * NB; };
+  auto ctr = [&](int i, int j, int s) { return a.cnt + ((size_t)j * MT + i) * Sp + s; };
+  auto rows_of = [&](int i) { return (int)min((int64_t)NB, a.m - (int64_t)i * NB); };
+  auto cols_of = [&](int j) { return (int)min((int64_t)NB, a.n - (int64_t)j * NB); };
+  for (;;) {
+    if (threadIdx.x == 0) {
+      int64_t t = -1;
+      if (!((volatile int*)&a.ctl->abort)[0]) t = (int64_t)atomicAdd(&a.ctl->ticket, 1u);
+      s_ticket = t;
+    }
+    __syncthreads();
+    const int64_t t = s_ticket;
+    if (t < 0 || t >= a.ntasks) break;
+    int type, sch, i, j, k;
+    decode_task(a.tasks[t], type, sch, i, j, k);
+    if (threadIdx.x == 0) {
+      bool ok = true;
+      const uint64_t to = a.timeout_ns;
+      switch (type) {
+        case TASK_GEQRT: ok = wait_ge(ctr(k, k, 0), Sp, (unsigned)k, a.ctl, to); break;
+        case TASK_UNMQR:
+          ok = wait_ge(ctr(k, k, 0), 1, (unsigned)k + 1, a.ctl, to) &&
+               wait_ge(ctr(k, j, sch), 1, (unsigned)k, a.ctl, to);
+          break;
+        case TASK_TSQRT:
+          ok = wait_ge(ctr(k, k, 0), Sp, (unsigned)i, a.ctl, to) &&
+               wait_ge(ctr(i, k, 0), Sp, (unsigned)k, a.ctl, to);
+          break;
+        default:
+          ok = wait_ge(ctr(i, k, 0), 1, (unsigned)k + 1, a.ctl, to) &&
+               wait_ge(ctr(k, j, sch), 1, (unsigned)i, a.ctl, to) &&
+               wait_ge(ctr(i, j, sch), 1, (unsigned)k, a.ctl, to);
+          break;
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int rk = rows_of(k), ck = cols_of(k);
+    switch (type) {
+      case TASK_GEQRT:
+        geqrt<S>(tile(k, k), NB, rk, ck, a.IB, tfac(k, k), sm, &a.ctl->status);
+        break;
+      case TASK_UNMQR: {
+        const int cj = cols_of(j);
+        const int c0 = (int)((int64_t)sch * cj / Sp), c1 = (int)((int64_t)(sch + 1) * cj / Sp);
+        unmqr<S>(tile(k, k), NB, tfac(k, k), a.IB, rk, ck, tile(k, j), NB, c0, c1, sm);
+        break;
+      }
+      case TASK_TSQRT:
+        tsqrt<S>(tile(k, k), NB, tile(i, k), NB, rows_of(i), ck, a.IB, tfac(i, k), sm, &a.ctl->status);
+        break;
+      default: {
+        const int cj = cols_of(j);
+        const int c0 = (int)((int64_t)sch * cj / Sp), c1 = (int)((int64_t)(sch + 1) * cj / Sp);
+        tsmqr<S>(tile(i, k), NB, tfac(i, k), a.IB, rows_of(i), ck, tile(k, j), NB, tile(i, j), NB, c0, c1, sm);
+        break;
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      switch (type) {
+        case TASK_GEQRT:
+          for (int s = 0; s < Sp; ++s) red_release_add(ctr(k, k, s), 1u);
+          break;
+        case TASK_UNMQR: red_release_add(ctr(k, j, sch), 1u); break;
+        case TASK_TSQRT:
+          for (int s = 0; s < Sp; ++s) {
+            red_release_add(ctr(k, k, s), 1u);
+            red_release_add(ctr(i, k, s), 1u);
+          }
+          break;
+        default:
+          red_release_add(ctr(k, j, sch), 1u);
+          red_release_add(ctr(i, j, sch), 1u);
+          break;
+      }
+    }
+  }
+}
+
+template <typename S>
+int persistent_grid(int* grid_out) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return (int)e;
+  const size_t smem = smem_elems<S>() * sizeof(S);
+  e = cudaFuncSetAttribute(persistent_qr<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_qr<S>, NTHREADS, smem);
+  if (e != cudaSuccess) return (int)e;
+  if (occ < 1) return (int)cudaErrorInvalidConfiguration;
+  int per = occ;
+  if (g_ctas_per_sm > 0) per = std::min(per, g_ctas_per_sm);
+  int grid = sms * per;
+  if (g_grid_limit > 0) grid = std::min(grid, g_grid_limit);
+  *grid_out = grid;
+  return 0;
+}
+
+template <typename S>
+int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, void* scratch,
+                int64_t scratch_bytes, void* stream) {
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (!A && m * n > 0) return -3;
+  if (lda < std::max<int64_t>(m, 1)) return -4;
+  if (nb == 0) {
+    if (qr_table_lookup(m, n, (int)sizeof(S), &nb, &ib) != 0) return -5;
+  }
+  if (nb < 8 || nb > 512) return -5;
+  if (ib < 1 || ib > nb || ib > 256) return -6;
+  if (m == 0 || n == 0) return 0;
+  if (!T) return -7;
+  if (!scratch) return -8;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const Layout L = make_layout(m, n, nb, ib, sizeof(S));
+  if (scratch_bytes < (int64_t)L.bytes) return -9;
+  if (L.MT > 65535 || L.NT > 65535) return -1;
+  const Sched& sc = get_schedule(L.MT, L.NT, L.S);
+  char* base = (char*)scratch;
+  DevCtl* ctl = (DevCtl*)base;
+  unsigned* cnt = (unsigned*)(base + L.off_cnt);
+  uint64_t* dtasks = (uint64_t*)(base + L.off_tasks);
+  S* W = (S*)(base + L.off_tiles);
+  int64_t ntasks = sc.n;
+  cudaError_t e;
+  if (g_drop_task >= 0 && g_drop_task < sc.n) {
+    // test hook: a task list with one task missing (host-made fault)
+    if (g_drop_task > 0)
+      e = cudaMemcpyAsync(dtasks, sc.host, sizeof(uint64_t) * g_drop_task, cudaMemcpyHostToDevice, st);
+    else
+      e = cudaSuccess;
+    if (e == cudaSuccess && g_drop_task + 1 < sc.n)
+      e = cudaMemcpyAsync(dtasks + g_drop_task, sc.host + g_drop_task + 1,
+                          sizeof(uint64_t) * (sc.n - g_drop_task - 1), cudaMemcpyHostToDevice, st);
+    ntasks = sc.n - 1;
+  } else {
+    e = cudaMemcpyAsync(dtasks, sc.host, sizeof(uint64_t) * sc.n, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return (int)e;
+  const int64_t nzero = (int64_t)(L.off_cnt / sizeof(unsigned)) + (int64_t)L.MT * L.NT * L.S;
+  cm_to_tiles<S><<<1184, 256, 0, st>>>(A, lda, m, n, W, nb, L.MT, L.NT, (unsigned*)base, nzero);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  int grid = 0;
+  int rc = persistent_grid<S>(&grid);
+  if (rc) return rc;
+  FactorArgs<S> fa;
+  fa.W = W; fa.T = T; fa.m = m; fa.n = n; fa.NB = nb; fa.IB = ib; fa.MT = L.MT; fa.NT = L.NT; fa.S_ = L.S;
+  fa.tasks = dtasks; fa.ntasks = ntasks; fa.cnt = cnt; fa.ctl = ctl;
+  fa.timeout_ns = (uint64_t)g_wait_timeout_us * 1000ull;
+  persistent_qr<S><<<grid, NTHREADS, smem_elems<S>() * sizeof(S), st>>>(fa);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  tiles_to_cm<S><<<1184, 256, 0, st>>>(W, A, lda, m, n, nb, L.MT);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int qr_workspace(int64_t m, int64_t n, int nb, int ib, int prec, int64_t* t_elems, int64_t* scratch_bytes) {
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (nb == 0) {
+    if (qr_table_lookup(m, n, prec == QR_PREC_F32 ? 4 : 8, &nb, &ib) != 0) return -3;
+  }
+  if (nb < 8 || nb > 512) return -3;
+  if (ib < 1 || ib > nb || ib > 256) return -4;
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -5;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const Layout L = make_layout(std::max<int64_t>(m, 1), std::max<int64_t>(n, 1), nb, ib,
+                               prec == QR_PREC_F64 ? 8 : 4);
+  if (t_elems) *t_elems = L.t_elems;
+  if (scratch_bytes) *scratch_bytes = (int64_t)L.bytes;
+  return 0;
+}
+
+int64_t qr_task_count(int64_t m, int64_t n, int nb, int ib) {
+  if (m <= 0 || n <= 0 || nb < 8) return 0;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const Layout L = make_layout(m, n, nb, ib, 8);
+  return L.ntasks;
+}
+
+int qr_factor_d(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* scratch,
+                int64_t scratch_bytes, void* stream) {
+  return factor_impl<double>(m, n, A, lda, nb, ib, T, scratch, scratch_bytes, stream);
+}
+
+int qr_factor_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, float* T, void* scratch,
+                int64_t scratch_bytes, void* stream) {
+  return factor_impl<float>(m, n, A, lda, nb, ib, T, scratch, scratch_bytes, stream);
+}
+
+int qr_status(const void* scratch, int* status, void* stream) {
+  if (!scratch) return -1;
+  if (!status) return -2;
+  DevCtl h;
+  cudaError_t e = cudaMemcpyAsync(&h, scratch, sizeof(DevCtl), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return (int)e;
+  *status = h.status;
+  return 0;
+}
+
+int qr_set_option(int opt, int64_t value) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  switch (opt) {
+    case QR_OPT_WAIT_TIMEOUT_US:
+      if (value <= 0) return -2;
+      g_wait_timeout_us = value;
+      return 0;
+    case QR_OPT_CTAS_PER_SM:
+      if (value < 0) return -2;
+      g_ctas_per_sm = (int)value;
+      return 0;
+    case QR_OPT_SPLIT:
+      if (value < 0 || value > 64) return -2;
+      g_split = (int)value;  // schedules are cached per split count
+      return 0;
+    case QR_OPT_GRID_LIMIT:
+      if (value < 0) return -2;
+      g_grid_limit = (int)value;
+      return 0;
+    case QR_OPT_DROP_TASK:
+      g_drop_task = value;
+      return 0;
+  }
+  return -1;
+}
+
+int64_t qr_get_option(int opt) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  switch (opt) {
+    case QR_OPT_WAIT_TIMEOUT_US: return g_wait_timeout_us;
+    case QR_OPT_CTAS_PER_SM: return g_ctas_per_sm;
+    case QR_OPT_SPLIT: return g_split;
+    case QR_OPT_GRID_LIMIT: return g_grid_limit;
+    case QR_OPT_DROP_TASK: return g_drop_task;
+  }
+  return INT64_MIN;
+}
+
+}  // extern "C"

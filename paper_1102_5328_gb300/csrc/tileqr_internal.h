@@ -1,0 +1,28 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+
+#include "../../include/tileqr.h"
+
+namespace tqr {
+
+enum TaskType { TASK_GEQRT = 0, TASK_UNMQR = 1, TASK_TSQRT = 2, TASK_TSMQR = 3 };
+
+// 64-bit task code: type (4 bits) | column chunk (12) | i (16) | j (16) | k (16)
+__host__ __device__ inline uint64_t encode_task(int type, int s, int i, int j, int k) {
+  return (uint64_t)(type & 0xF) | ((uint64_t)(s & 0xFFF) << 4) | ((uint64_t)(i & 0xFFFF) << 16) |
+         ((uint64_t)(j & 0xFFFF) << 32) | ((uint64_t)(k & 0xFFFF) << 48);
+}
+__host__ __device__ inline void decode_task(uint64_t c, int& type, int& s, int& i, int& j, int& k) {
+  type = (int)(c & 0xF);
+  s = (int)((c >> 4) & 0xFFF);
+  i = (int)((c >> 16) & 0xFFFF);
+  j = (int)((c >> 32) & 0xFFFF);
+  k = (int)((c >> 48) & 0xFFFF);
+}
+
+}  // namespace tqr
+
+// (nb, ib) for a shape from the loaded tuning table (nearest tuned N), or the
+// built-in default when no table is loaded. Returns 0 on success.
+int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib);

@@ -63,3 +63,16 @@ def batch_matrices(ms, ns, seed, dtype=np.float64):
     for m, n in zip(ms, ns):
         out.append(np.asfortranarray(rng.standard_normal((int(n), int(m))).T.astype(dtype)))
     return out
+
+
+def mlp_init(seed, layers=((4, 64), (64, 64), (64, 1))):
+    """Initial weights of the cost-model MLP: each Linear(in, out) draws
+    W (out x in, row-major) and b (out) uniform in [-1/sqrt(in), 1/sqrt(in)]
+    from one seeded stream. Returns [W1, b1, W2, b2, W3, b3] as float64."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for fin, fout in layers:
+        bound = 1.0 / np.sqrt(fin)
+        out.append(rng.uniform(-bound, bound, size=(fout, fin)))
+        out.append(rng.uniform(-bound, bound, size=(fout,)))
+    return out

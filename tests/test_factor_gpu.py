@@ -1,0 +1,154 @@
+"""GPU parity of the tile QR (C ABI: qr_factor_d, qr_apply_qt_d) against the
+CPU oracle: backward error, orthogonality, |R| up to row signs, exact sign
+agreement on a single tile, determinism, and host-made faults."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle
+from paper_1102_5328_gb300 import inputs
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1102_5328_gb300 as q
+    q.lib()
+    return q
+
+
+def to_dev(x):
+    """Column-major CUDA copy of a NumPy matrix."""
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x).T)).cuda().t()
+
+
+def _gpu_factor(q, A_np, nb, ib):
+    A = to_dev(A_np)
+    f = q.qr_factor(A, nb, ib)
+    torch.cuda.synchronize()
+    return f
+
+
+def _check(q, A_np, nb, ib, r_tol=1e-10):
+    m, n = A_np.shape
+    f = _gpu_factor(q, A_np, nb, ib)
+    assert f.status() == 0
+    R = np.triu(f.A[:n].cpu().numpy())
+    Q = q.form_q(f).cpu().numpy()
+    torch.cuda.synchronize()
+    res = oracle.fact_residual(A_np, Q, R) / (n * U)
+    orth = oracle.orth_residual(Q) / (n * U)
+    assert res <= 10.0, res
+    assert orth <= 10.0, orth
+    F, _ = oracle.geqr2(A_np)
+    R_or = np.triu(F[:n])
+    D = oracle.row_signs(R, R_or)
+    rel = np.linalg.norm(D[:, None] * R - R_or) / np.linalg.norm(R_or)
+    assert rel <= r_tol, rel
+    return f, R, R_or
+
+
+def test_single_tile_matches_oracle_signs(q):
+    """NB >= max(m, n): tile QR is one GEQRT, the blocked Householder QR with
+    the oracle's sign convention, so R and the reflectors match directly."""
+    A = inputs.uniform_matrix(128, 128, seed=3)
+    f, R, R_or = _check(q, A, 128, 32)
+    assert np.array_equal(np.sign(np.diag(R)), np.sign(np.diag(R_or)))
+    assert np.abs(R - R_or).max() <= 1e-13 * np.abs(R_or).max()
+    F, tau = oracle.geqr2(A)
+    V = np.tril(f.A.cpu().numpy(), -1)
+    assert np.abs(V - np.tril(F, -1)).max() < 1e-12
+    # T's diagonal holds tau (IB x NB block factors, ld IB)
+    T = f.T[: 32 * 128].cpu().numpy().reshape(128, 32).T
+    taus = np.array([T[p % 32, p] for p in range(128)])
+    assert np.abs(taus - tau).max() < 1e-13
+
+
+@pytest.mark.parametrize("m,n,nb,ib", [
+    (512, 512, 128, 32),    # the 512 x 512, NB = 128, IB = 32 case
+    (300, 200, 64, 16),
+    (1000, 1000, 96, 32),   # NB does not divide N: ragged edge tiles
+    (700, 300, 128, 9),     # odd IB, ragged inner blocks
+    (513, 513, 256, 128),   # IB > 32: level-2 sub-panels inside a block
+    (640, 600, 512, 256),   # largest IB, split update tasks
+    (450, 450, 160, 80),
+    (257, 129, 32, 8),
+    (64, 64, 64, 32),
+    (100, 1, 32, 8),        # a single column
+    (33, 33, 8, 8),
+])
+def test_factor_parity(q, m, n, nb, ib):
+    A = inputs.uniform_matrix(m, n, seed=m * 7 + n)
+    _check(q, A, nb, ib)
+
+
+def test_apply_qt_is_transpose(q):
+    m, n = 400, 300
+    A = inputs.uniform_matrix(m, n, seed=9)
+    f = _gpu_factor(q, A, 64, 16)
+    C = to_dev(inputs.normal_matrix(m, 5, seed=2))
+    C0 = C.clone()
+    q.qr_apply_qt(f, C, trans=True)
+    # Q^T A = [R; 0]
+    Ad = to_dev(A)
+    q.qr_apply_qt(f, Ad, trans=True)
+    R = torch.triu(f.A[:n]).cpu().numpy()
+    QtA = Ad.cpu().numpy()
+    assert np.abs(QtA[:n] - R).max() < 50 * n * U
+    assert np.abs(QtA[n:]).max() < 50 * n * U
+    q.qr_apply_qt(f, C, trans=False)
+    assert torch.allclose(C, C0, atol=100 * n * U, rtol=0)
+
+
+def test_deterministic_and_schedule_independent(q):
+    """The DAG fixes every tile's operation sequence, so the result is bitwise
+    identical run to run and with one CTA running the tasks sequentially."""
+    A = inputs.uniform_matrix(777, 600, seed=4)
+    f1 = _gpu_factor(q, A, 96, 24)
+    f2 = _gpu_factor(q, A, 96, 24)
+    assert torch.equal(f1.A, f2.A) and torch.equal(f1.T, f2.T)
+    q.qr_set_option(q.QR_OPT_GRID_LIMIT, 1)
+    try:
+        f3 = _gpu_factor(q, A, 96, 24)
+    finally:
+        q.qr_set_option(q.QR_OPT_GRID_LIMIT, 0)
+    assert torch.equal(f1.A, f3.A) and torch.equal(f1.T, f3.T)
+
+
+def test_missing_task_times_out_with_status(q):
+    """Host-made fault: drop one task from the list; its dependents' bounded
+    waits expire, the kernel returns, the status word says so, and the
+    context stays usable."""
+    A = inputs.uniform_matrix(256, 256, seed=5)
+    q.qr_set_option(q.QR_OPT_WAIT_TIMEOUT_US, 200_000)
+    q.qr_set_option(q.QR_OPT_DROP_TASK, 3)
+    try:
+        f = _gpu_factor(q, A, 64, 16)
+        st = f.status()
+    finally:
+        q.qr_set_option(q.QR_OPT_DROP_TASK, -1)
+        q.qr_set_option(q.QR_OPT_WAIT_TIMEOUT_US, 20_000_000)
+    assert st & q.QR_DEV_TIMEOUT
+    _check(q, A, 64, 16)
+
+
+def test_nonfinite_input_flagged(q):
+    A = inputs.uniform_matrix(128, 128, seed=6)
+    A[5, 0] = np.nan
+    f = _gpu_factor(q, A, 64, 16)
+    assert f.status() & q.QR_DEV_NONFINITE
+
+
+def test_invalid_arguments_rejected(q):
+    A = q.colmajor_empty(100, 50, torch.float64)
+    lib = q.lib()
+    import ctypes
+    assert lib.qr_factor_d(100, 50, ctypes.c_void_p(A.data_ptr()), 99, 32, 8, None, None, 0, None) == -4
+    assert lib.qr_factor_d(100, 50, ctypes.c_void_p(A.data_ptr()), 100, 600, 8, None, None, 0, None) == -5
+    assert lib.qr_factor_d(100, 50, ctypes.c_void_p(A.data_ptr()), 100, 32, 33, None, None, 0, None) == -6
+    assert lib.qr_factor_d(50, 100, ctypes.c_void_p(A.data_ptr()), 100, 32, 8, None, None, 0, None) == -2
