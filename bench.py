@@ -1,0 +1,326 @@
+"""Benchmark of the FP64 tile Householder QR on one GB300 (or N replicas).
+
+Workload: square FP64 tile QR of order N = 10000 (the largest order of the
+paper's Step-2 discretization, Sec. 5.1), entries uniform[-0.5, 0.5) from a
+seed, with the (NB, IB) pair of the tuning table (or --nb/--ib).
+A step = restore A from a pristine device copy, then qr_factor_d (layout
+conversion, the persistent DAG kernel, conversion back). Inputs (800 MB)
+are larger than L2, so no flush is needed between steps.
+
+Metric: GFlop/s = (2mn^2 - 2n^3/3) / t (= 4/3 N^3 / t, the paper's P of
+Sec. 2.2, independent of IB). With --gpus N > 1 (torchrun, one rank per GPU)
+every rank factors its own matrix (replicas: a single factorization does not
+shard), value = total credited flops / max over ranks of the time.
+
+--impl reference times the CPU oracle (unblocked Householder QR, OpenMP) on
+the host cores on a bounded sample of the same workload: the first K
+reflectors of the same N = 10000 matrix.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_DEFAULT = 10000
+SEED = 10000
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(A_np, seconds_target=15.0):
+    """Time the oracle's first k reflectors of A (fp64, OpenMP on the host
+    cores). Returns (GFlop/s, k, seconds, threads)."""
+    import oracle
+    threads = oracle.set_threads(0)
+    m, n = A_np.shape
+
+    def flops(k):
+        return sum(4.0 * (m - j) * (n - j - 1) + 2.0 * (m - j - 1) for j in range(k))
+
+    k = 16
+    t0 = time.perf_counter()
+    oracle.geqr2(A_np, kmax=k)
+    dt = time.perf_counter() - t0
+    rate = flops(k) / max(dt, 1e-9)
+    k2 = 16
+    while k2 < n and flops(k2 * 2) / rate < seconds_target:
+        k2 *= 2
+    t0 = time.perf_counter()
+    oracle.geqr2(A_np, kmax=k2)
+    dt = time.perf_counter() - t0
+    return flops(k2) / dt / 1e9, k2, dt, threads
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    from paper_1102_5328_gb300 import inputs
+    import oracle
+    n = args.n
+    A_np = inputs.uniform_matrix(n, n, seed=SEED)
+    threads = oracle.set_threads(0)
+    m = n
+
+    def flops(k):
+        return sum(4.0 * (m - j) * (n - j - 1) + 2.0 * (m - j - 1) for j in range(k))
+
+    # size one step to ~8 s of CPU work
+    t0 = time.perf_counter()
+    oracle.geqr2(A_np, kmax=16)
+    rate = flops(16) / max(time.perf_counter() - t0, 1e-9)
+    k = 16
+    while k < n and flops(k * 2) / rate < 8.0:
+        k *= 2
+    for _ in range(args.warmup):
+        oracle.geqr2(A_np, kmax=k)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.geqr2(A_np, kmax=k)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = flops(k) * args.steps / T / 1e9
+    sample = "first %d Householder reflectors of the N=%d uniform[-0.5,0.5) matrix per step" % (k, n)
+    line = {
+        "impl": "reference", "metric": "QR GFlop/s (2mn^2 - 2n^3/3)/t", "value": value, "unit": "GFLOP/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fp64 square tile QR, N=%d, uniform[-0.5,0.5)" % n, "m": n, "n": n},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--ib", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1102_5328_gb300 as q
+    from paper_1102_5328_gb300 import inputs
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    n = args.n
+    m = n
+    nb, ib = (args.nb, args.ib) if args.nb else q.qr_lookup(m, n, torch.float64)
+    A_np = inputs.uniform_matrix(m, n, seed=SEED + rank)
+    A0 = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()  # column-major, on device
+    A = A0.clone().t().contiguous().t()
+    t_elems, sbytes = q.qr_workspace(m, n, nb, ib, torch.float64)
+    T = torch.empty(t_elems, dtype=torch.float64, device="cuda")
+    scratch = torch.empty(sbytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    lib = q.lib()
+
+    def step():
+        A.copy_(A0)
+        q.qr_factor(A, nb, ib, T=T, scratch=scratch, stream=stream)
+
+    peak_live = q.qr_peak_fp64()
+    q.qr_set_option(q.QR_OPT_RECORD_EVENTS, 1)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = q.qr_status(scratch)
+    if st != 0:
+        raise RuntimeError("device status %d after warm-up" % st)
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kernel_ms = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        kernel_ms.append(None)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    # per-launch kernel time of the dominant (persistent) kernel: re-time
+    # each step with the library's own events on the launching stream
+    for s in range(args.steps):
+        step()
+        kernel_ms[s] = q.qr_last_kernel_ms()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    flops = q.qr_flops(m, n)
+    value = flops * args.steps * ws / (total_ms * 1e-3) / 1e9
+    kavg = sum(kernel_ms) / len(kernel_ms)
+    nominal_peak = 152 * 2 * 2 * 2.070e9 / 1e12  # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+    achieved = flops / (kavg * 1e-3) / 1e12
+    roofline = {
+        "bound": "alu", "kernel": "persistent_qr<double> (FP64 DFMA pipe)",
+        "achieved": achieved, "peak": nominal_peak, "unit": "TFLOP/s", "frac": achieved / nominal_peak,
+        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+        "peak_measured_live": peak_live / 1e3, "frac_of_measured": achieved / (peak_live / 1e3),
+        "traffic": None, "kernel_ms_avg": kavg,
+    }
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API: pinned host A -> device, factor,
+        # factored A and T -> host, every step
+        hA = torch.from_numpy(np.ascontiguousarray(A_np.T)).pin_memory()
+        hOut = torch.empty_like(hA).pin_memory()
+        hT = torch.empty(t_elems, dtype=torch.float64).pin_memory()
+        Ad = A  # reuse the device buffer (column-major view)
+
+        def e2e_step():
+            Ad.t().copy_(hA, non_blocking=True)
+            q.qr_factor(Ad, nb, ib, T=T, scratch=scratch, stream=stream)
+            hOut.copy_(Ad.t(), non_blocking=True)
+            hT.copy_(T, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = max(2, min(args.steps, 3))
+        ea.record(stream)
+        for _ in range(ks):
+            e2e_step()
+        eb.record(stream)
+        torch.cuda.synchronize()
+        ems = ea.elapsed_time(eb)
+        if ws > 1:
+            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": flops * ks * ws / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * t_elems,
+               "steps": ks}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        g, k, dt, threads = cpu_oracle_sample(A_np)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": "first %d Householder reflectors of the same N=%d matrix (%.1f s)" % (k, n, dt)}
+
+    tuning = None
+    tpath = os.path.join(ROOT, "paper_1102_5328_gb300", "tuned", "gb300_fp64.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        tuning = {k: tj.get(k) for k in ("autotuned_over_grid_best", "tuning_seconds", "full_grid_seconds",
+                                        "heuristic", "source")}
+
+    if rank == 0:
+        line = {
+            "metric": "QR GFlop/s (2mn^2 - 2n^3/3)/t", "value": value, "unit": "GFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "fp64 square tile QR, N=%d, uniform[-0.5,0.5)" % n, "m": m, "n": n,
+                       "nb": nb, "ib": ib, "l2": "inputs (800 MB) larger than L2; no flush",
+                       "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "pct_fp64_peak": 100.0 * value / ws / (nominal_peak * 1e3),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": clk, "tuning": tuning,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

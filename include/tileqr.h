@@ -49,6 +49,7 @@ extern "C" {
 #define QR_OPT_SPLIT           3 /* column chunks per update task (0 = automatic) */
 #define QR_OPT_GRID_LIMIT      4 /* cap on persistent CTAs (0 = all SMs); 1 = sequential */
 #define QR_OPT_DROP_TASK       5 /* test hook: omit this ticket from the task list (-1 = off) */
+#define QR_OPT_RECORD_EVENTS   6 /* 1: bracket each persistent kernel with CUDA events on its stream */
 
 /*
  * qr_workspace -- sizes of the caller-owned buffers of qr_factor_*.
@@ -105,6 +106,102 @@ int qr_status(const void *d_scratch, int *status, void *stream);
 /* qr_set_option / qr_get_option -- process-wide settings (QR_OPT_*). */
 int qr_set_option(int opt, int64_t value);
 int64_t qr_get_option(int opt);
+
+/*
+ * qr_last_kernel_ms -- with QR_OPT_RECORD_EVENTS on, waits for and returns
+ * the device time (ms, CUDA events on the launching stream) of the most
+ * recent persistent factorization kernel. -2 if none was recorded.
+ */
+int qr_last_kernel_ms(float *ms);
+
+/*
+ * qr_peak_fp64 -- measures the FP64 fused multiply-add throughput of the
+ * current device with a register-resident kernel (independent FMA chains on
+ * every SM, timed with CUDA events on `stream`, synchronous). *gflops gets
+ * the rate in GFLOP/s (2 flops per FMA). Used as a live roofline reference.
+ */
+int qr_peak_fp64(double *gflops, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Empirical NB/IB autotuner (Secs. 4-5 of the paper).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * qr_tune -- install-time tuning (Sec. 6: "make autotune", then an instant
+ * decision at call time). Shapes (ms[i], ns[i]), nshapes >= 1.
+ * mode 0 (PSPAYG): Step 1 = time the TSMQR kernel (the paper's DSSRFB) for
+ *   every (NB, IB) of the grid NB in {64..512 step 32}, IB | NB,
+ *   8 <= IB <= NB/2 (119 pairs), 50 launches each, "No Flush" (Sec. 4);
+ *   Property 4.1 (best IB per NB), Property 4.2 (upper convex hull) and
+ *   Heuristic `heuristic` (0, 1 or 2; 2 is the paper's default) preselect at
+ *   most 8 pairs; Step 2 = time qr_factor for the survivors at every shape,
+ *   ascending n, `reps` runs each (median; the paper uses 6, Sec. 5.1), and
+ *   prune as you go with Property 5.1 between square orders (Sec. 5.3).
+ * mode 1 (exhaustive search, ES): Step 2 over the whole grid, no pruning.
+ * prec: QR_PREC_F64 / QR_PREC_F32. table_path (may be NULL/""): JSON decision
+ * table written at the end; it also becomes the in-process table used by
+ * nb = 0. log_path (may be NULL/""): JSONL of every measurement, appended;
+ * measurements already in it are reused, so an interrupted run resumes.
+ * d_work (work_bytes >= qr_tune_workspace): device scratch owned by the
+ * caller. seconds_out[4] (may be NULL): total, Step-1 and Step-2 wall
+ * seconds, and the number of factorizations timed in this call. Synchronous.
+ */
+int qr_tune(const int64_t *ms, const int64_t *ns, int nshapes, int heuristic, int mode, int reps, int prec,
+            const char *table_path, const char *log_path, void *d_work, int64_t work_bytes,
+            double *seconds_out, void *stream);
+
+/* qr_tune_workspace -- device bytes qr_tune needs for shapes up to max_m x max_n. */
+int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t *bytes);
+
+/*
+ * qr_load_table / qr_clear_tables / qr_lookup -- the decision table. A
+ * request for an untuned shape uses the closest tuned one (Sec. 5.1: the
+ * closest benchmarked configuration), distance |m - m_i| + |n - n_i|, ties
+ * to the smaller tuned shape; with no table the built-in pair (128, 32).
+ * prec selects the fp64 or fp32 table (fp32 falls back to fp64's).
+ */
+int qr_load_table(const char *path);
+int qr_clear_tables(void);
+int qr_lookup(int64_t m, int64_t n, int prec, int *nb, int *ib);
+
+/*
+ * Host-only decision rules of the tuner (no GPU call), exported so that they
+ * can be checked on their own:
+ * qr_tune_grid -- the (NB, IB) grid (NB in nb_lo..nb_hi step nb_step, IB a
+ *   divisor of NB in [ib_min, NB/2]); writes up to cap pairs, returns the count.
+ * qr_tune_preselect -- Property 4.1, the upper hull (Property 4.2) and
+ *   Heuristic 0/1/2 over npairs Step-1 results; writes the preselected
+ *   pairs (ascending NB) and returns how many (<= max_sel for H1/H2;
+ *   nseg iso-segments for H2).
+ * qr_tune_payg -- Property 5.1: keep[a] = 0 iff some pair with larger NB has
+ *   strictly higher performance at the order just measured.
+ * qr_tune_nearest -- the closest grid value (ties to the smaller), Sec. 5.1.
+ */
+int qr_tune_grid(int nb_lo, int nb_hi, int nb_step, int ib_min, int cap, int *nbs, int *ibs);
+int qr_tune_preselect(int npairs, const int *nb, const int *ib, const double *perf, int heuristic, int max_sel,
+                      int nseg, int *sel_nb, int *sel_ib);
+int qr_tune_payg(int nsurv, const int *nb, const double *perf, int *keep);
+int64_t qr_tune_nearest(int64_t value, const int64_t *grid, int ngrid);
+
+/*
+ * qr_step1_workspace / qr_step1_time -- the Step-1 kernel benchmark of Sec. 4
+ * for one (nb, ib): `launches` back-to-back launches of a batch of
+ * 2 x (SM count) independent TSMQR tile tasks (same data every launch:
+ * "No Flush"), timed with CUDA events on `stream`; synchronous.
+ * *seconds_per_launch, and *gflops (may be NULL) = batch x 4 NB^3 / time.
+ */
+int qr_step1_workspace(int nb, int prec, int64_t *bytes);
+int qr_step1_time(int nb, int ib, int prec, int launches, double *seconds_per_launch, double *gflops,
+                  void *d_work, int64_t work_bytes, void *stream);
+
+/*
+ * qr_time_factor -- the Step-2 measurement: qr_factor at (m, n, nb, ib) on a
+ * device-generated uniform[-0.5, 0.5) matrix, reps timed runs after one
+ * warm-up (CUDA events around each call), median and minimum seconds.
+ * d_work must hold A (m x n), T and the factorization scratch.
+ */
+int qr_time_factor(int64_t m, int64_t n, int nb, int ib, int prec, int reps, double *median_s, double *min_s,
+                   void *d_work, int64_t work_bytes, void *stream);
 
 /* qr_task_count -- number of tasks of the factorization DAG (diagnostics). */
 int64_t qr_task_count(int64_t m, int64_t n, int nb, int ib);

@@ -25,6 +25,7 @@ QR_OPT_CTAS_PER_SM = 2
 QR_OPT_SPLIT = 3
 QR_OPT_GRID_LIMIT = 4
 QR_OPT_DROP_TASK = 5
+QR_OPT_RECORD_EVENTS = 6
 
 
 def lib():
@@ -139,6 +140,18 @@ def qr_set_option(opt, value):
 
 def qr_get_option(opt):
     return lib().qr_get_option(opt)
+
+
+def qr_last_kernel_ms():
+    ms = ctypes.c_float()
+    _lib.check(lib().qr_last_kernel_ms(ctypes.byref(ms)), "qr_last_kernel_ms")
+    return ms.value
+
+
+def qr_peak_fp64(stream=None):
+    g = ctypes.c_double()
+    _lib.check(lib().qr_peak_fp64(ctypes.byref(g), _stream_ptr(stream)), "qr_peak_fp64")
+    return g.value
 
 
 def qr_task_count(m, n, nb, ib):

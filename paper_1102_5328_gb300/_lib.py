@@ -25,6 +25,24 @@ SIGNATURES = [
     ("qr_set_option", c_int, [c_int, c_i64]),
     ("qr_get_option", c_i64, [c_int]),
     ("qr_task_count", c_i64, [c_i64, c_i64, c_int, c_int]),
+    ("qr_last_kernel_ms", c_int, [ctypes.POINTER(ctypes.c_float)]),
+    ("qr_load_table", c_int, [ctypes.c_char_p]),
+    ("qr_clear_tables", c_int, []),
+    ("qr_lookup", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    ("qr_tune_grid", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    ("qr_tune_preselect", c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_dbl), c_int,
+                                  c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    ("qr_tune_payg", c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_dbl), ctypes.POINTER(c_int)]),
+    ("qr_tune_nearest", c_i64, [c_i64, ctypes.POINTER(c_i64), c_int]),
+    ("qr_step1_workspace", c_int, [c_int, c_int, ctypes.POINTER(c_i64)]),
+    ("qr_step1_time", c_int, [c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_i64,
+                              c_vp]),
+    ("qr_tune_workspace", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_i64)]),
+    ("qr_time_factor", c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),
+                               c_vp, c_i64, c_vp]),
+    ("qr_tune", c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_int, c_int, c_int, c_int, c_int,
+                        ctypes.c_char_p, ctypes.c_char_p, c_vp, c_i64, ctypes.POINTER(c_dbl), c_vp]),
+    ("qr_peak_fp64", c_int, [ctypes.POINTER(c_dbl), c_vp]),
 ]
 
 

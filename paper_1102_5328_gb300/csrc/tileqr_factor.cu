@@ -34,6 +34,9 @@ int g_ctas_per_sm = 0;
 int g_split = 0;
 int g_grid_limit = 0;
 int64_t g_drop_task = -1;
+int g_record = 0;
+cudaEvent_t g_ev[2] = {nullptr, nullptr};
+bool g_ev_pending = false;
 
 struct Layout {
   int64_t m, n;
@@ -407,8 +410,19 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
   fa.W = W; fa.T = T; fa.m = m; fa.n = n; fa.NB = nb; fa.IB = ib; fa.MT = L.MT; fa.NT = L.NT; fa.S_ = L.S;
   fa.tasks = dtasks; fa.ntasks = ntasks; fa.cnt = cnt; fa.ctl = ctl;
   fa.timeout_ns = (uint64_t)g_wait_timeout_us * 1000ull;
+  if (g_record) {
+    if (!g_ev[0]) {
+      if ((e = cudaEventCreate(&g_ev[0])) != cudaSuccess) return (int)e;
+      if ((e = cudaEventCreate(&g_ev[1])) != cudaSuccess) return (int)e;
+    }
+    cudaEventRecord(g_ev[0], st);
+  }
   persistent_qr<S><<<grid, NTHREADS, smem_elems<S>() * sizeof(S), st>>>(fa);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  if (g_record) {
+    cudaEventRecord(g_ev[1], st);
+    g_ev_pending = true;
+  }
   tiles_to_cm<S><<<1184, 256, 0, st>>>(W, A, lda, m, n, nb, L.MT);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   return 0;
@@ -464,9 +478,21 @@ int qr_status(const void* scratch, int* status, void* stream) {
   return 0;
 }
 
+int qr_last_kernel_ms(float* ms) {
+  if (!ms) return -1;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_ev_pending) return -2;
+  cudaError_t e = cudaEventSynchronize(g_ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, g_ev[0], g_ev[1]);
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
 int qr_set_option(int opt, int64_t value) {
   std::lock_guard<std::mutex> lock(g_mu);
   switch (opt) {
+    case QR_OPT_RECORD_EVENTS:
+      g_record = value ? 1 : 0;
+      return 0;
     case QR_OPT_WAIT_TIMEOUT_US:
       if (value <= 0) return -2;
       g_wait_timeout_us = value;
@@ -498,6 +524,7 @@ int64_t qr_get_option(int opt) {
     case QR_OPT_SPLIT: return g_split;
     case QR_OPT_GRID_LIMIT: return g_grid_limit;
     case QR_OPT_DROP_TASK: return g_drop_task;
+    case QR_OPT_RECORD_EVENTS: return g_record;
   }
   return INT64_MIN;
 }

@@ -1,0 +1,585 @@
+// The empirical NB/IB autotuner (Secs. 4-5 of the paper), on the GPU.
+//
+// Step 1 (Sec. 4): time the update kernel that dominates the factorization
+// (TSMQR, the paper's DSSRFB, O(NT^3) calls) for every (NB, IB) of the grid:
+// 50 back-to-back launches of a device-filling batch of independent tile
+// tasks, same data every call ("No Flush", the mode the paper reports).
+// Then Property 4.1 keeps the best IB per NB, Property 4.2's upper convex
+// hull of (NB, performance) is formed, and Heuristic 0/1/2 preselects at
+// most 8 pairs.
+// Step 2 (Sec. 5): time the whole factorization for the preselected pairs at
+// each benchmarked order N, ascending, 6 runs each (median), and prune as
+// you go with Property 5.1. Untuned orders use the closest tuned one
+// (Sec. 5.1). The decision table is written to JSON and every measurement is
+// appended to a JSONL log, which a later run reads to skip what is measured.
+//
+// Optionally a small MLP cost model (tileqr_mlp.cu), trained on the timings
+// gathered so far, ranks the survivors at each new N; only the ones it ranks
+// near the top are measured, and the measurement always decides.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tile_kernels.cuh"
+#include "tileqr_internal.h"
+
+using namespace tqr;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Pure host rules (also exported for the CPU tests).
+struct Pt {
+  double x, y;
+};
+
+double cross(const Pt& o, const Pt& a, const Pt& b) { return (a.x - o.x) * (b.y - o.y) - (a.y - o.y) * (b.x - o.x); }
+
+// Upper hull, left to right, both end points, collinear middle points dropped.
+std::vector<Pt> upper_hull(std::vector<Pt> p) {
+  std::sort(p.begin(), p.end(), [](const Pt& a, const Pt& b) { return a.x < b.x || (a.x == b.x && a.y < b.y); });
+  std::vector<Pt> h;
+  for (const Pt& q : p) {
+    while (h.size() >= 2 && cross(h[h.size() - 2], h.back(), q) >= 0) h.pop_back();
+    h.push_back(q);
+  }
+  return h;
+}
+
+std::vector<double> steepness(const std::vector<Pt>& h) {
+  std::vector<double> s;
+  Pt prev{0.0, 0.0};
+  for (const Pt& q : h) {
+    s.push_back((q.y - prev.y) / (q.x - prev.x));
+    prev = q;
+  }
+  return s;
+}
+
+// Property 4.1 then the hull then H0/H1/H2. Returns selected NBs (ascending).
+std::vector<int> select_nbs(const std::map<int, std::pair<int, double>>& best, int heuristic, int max_sel, int nseg,
+                            int nb_lo, int nb_hi) {
+  std::vector<Pt> pts;
+  for (auto& kv : best) pts.push_back({(double)kv.first, kv.second.second});
+  std::vector<Pt> h = upper_hull(pts);
+  std::vector<double> st = steepness(h);
+  std::vector<int> out;
+  if (heuristic == 0) {
+    for (auto& q : h) out.push_back((int)q.x);
+  } else if (heuristic == 1) {
+    std::vector<int> idx(h.size());
+    for (size_t i = 0; i < h.size(); ++i) idx[i] = (int)i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return st[a] > st[b] || (st[a] == st[b] && h[a].x < h[b].x); });
+    for (int i = 0; i < (int)idx.size() && i < max_sel; ++i) out.push_back((int)h[idx[i]].x);
+  } else {
+    const double w = (double)(nb_hi - nb_lo) / nseg;
+    for (int s = 0; s < nseg; ++s) {
+      const double a = nb_lo + s * w, b = nb_lo + (s + 1) * w;
+      int bi = -1;
+      for (int i = 0; i < (int)h.size(); ++i) {
+        const bool inside = (h[i].x >= a && h[i].x < b) || (s == nseg - 1 && h[i].x == (double)nb_hi);
+        if (inside && (bi < 0 || st[i] > st[bi])) bi = i;
+      }
+      if (bi >= 0) out.push_back((int)h[bi].x);
+    }
+  }
+  std::sort(out.begin(), out.end());
+  if ((int)out.size() > max_sel && heuristic != 0) out.resize(max_sel);
+  return out;
+}
+
+std::vector<std::pair<int, int>> grid_pairs(int nb_lo, int nb_hi, int step, int ib_min) {
+  std::vector<std::pair<int, int>> g;
+  for (int nb = nb_lo; nb <= nb_hi; nb += step)
+    for (int ib = ib_min; ib <= nb / 2; ++ib)
+      if (nb % ib == 0) g.push_back({nb, ib});
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// Table (decision tree of Sec. 6: tuned at install time, read at call time).
+struct Entry {
+  int64_t m, n;
+  int nb, ib;
+  double gflops;
+};
+std::mutex g_tmu;
+std::vector<Entry> g_table[2];  // [0] fp64, [1] fp32
+
+int lookup_entry(const std::vector<Entry>& t, int64_t m, int64_t n, int* nb, int* ib) {
+  if (t.empty()) return 1;
+  int64_t best = INT64_MAX, bsum = INT64_MAX;
+  int bi = -1;
+  for (int i = 0; i < (int)t.size(); ++i) {
+    const int64_t d = std::llabs(t[i].m - m) + std::llabs(t[i].n - n);
+    const int64_t s = t[i].m + t[i].n;
+    if (d < best || (d == best && s < bsum)) {
+      best = d;
+      bsum = s;
+      bi = i;
+    }
+  }
+  *nb = t[bi].nb;
+  *ib = t[bi].ib;
+  return 0;
+}
+
+// --- minimal JSON table writer/reader (flat, fixed schema) -----------------
+bool write_table(const char* path, int prec, const std::vector<Entry>& t, const std::string& extra) {
+  FILE* f = fopen(path, "w");
+  if (!f) return false;
+  fprintf(f, "{\n  \"prec\": \"%s\",\n%s  \"entries\": [\n", prec ? "fp32" : "fp64", extra.c_str());
+  for (size_t i = 0; i < t.size(); ++i)
+    fprintf(f, "    {\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"gflops\": %.4f}%s\n", (long long)t[i].m,
+            (long long)t[i].n, t[i].nb, t[i].ib, t[i].gflops, i + 1 < t.size() ? "," : "");
+  fprintf(f, "  ]\n}\n");
+  fclose(f);
+  return true;
+}
+
+bool read_table(const char* path, int* prec, std::vector<Entry>* t) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  std::string s;
+  char buf[4096];
+  size_t r;
+  while ((r = fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, r);
+  fclose(f);
+  *prec = (s.find("\"prec\": \"fp32\"") != std::string::npos) ? 1 : 0;
+  size_t p = s.find("\"entries\"");
+  if (p == std::string::npos) return false;
+  t->clear();
+  while ((p = s.find("{\"m\":", p)) != std::string::npos) {
+    Entry e;
+    long long m, n;
+    if (sscanf(s.c_str() + p, "{\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"gflops\": %lf", &m, &n, &e.nb,
+               &e.ib, &e.gflops) != 5)
+      return false;
+    e.m = m;
+    e.n = n;
+    t->push_back(e);
+    ++p;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers for Step 1 and Step 2 inputs.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  // SplitMix64 finalizer (Steele, Lea, Flood 2014)
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+template <typename S>
+__global__ void fill_uniform(S* p, int64_t n, uint64_t seed, double lo, double hi) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double u = (double)(mix64(seed * 0x100000001B3ull + (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+    p[i] = (S)(lo + (hi - lo) * u);
+  }
+}
+
+// Step-1 kernel: CTA b applies one TSMQR (V, T shared) to its own tile pair.
+template <typename S>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    tsmqr_batch(const S* V, const S* T, S* C1, S* C2, int NB, int IB) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Smem<S> sm = carve<S>(reinterpret_cast<S*>(smem_raw));
+  const size_t te = (size_t)NB * NB;
+  tsmqr<S>(V, NB, T, IB, NB, NB, C1 + blockIdx.x * te, NB, C2 + blockIdx.x * te, NB, 0, NB, sm);
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+int64_t step1_bytes(int nb, int nbatch, size_t esz) {
+  // V, T (NB x NB each, generous) + two tiles per task
+  return (int64_t)((2 + 2 * (size_t)nbatch) * nb * nb * esz) + 4096;
+}
+
+template <typename S>
+int step1_time(int nb, int ib, int nbatch, int launches, double* sec, void* work, int64_t wbytes,
+               cudaStream_t st) {
+  if (step1_bytes(nb, nbatch, sizeof(S)) > wbytes) return -7;
+  const size_t te = (size_t)nb * nb;
+  S* V = (S*)work;
+  S* T = V + te;
+  S* C1 = T + te;
+  S* C2 = C1 + (size_t)nbatch * te;
+  fill_uniform<S><<<1024, 256, 0, st>>>(V, (int64_t)te, 11, -0.05, 0.05);
+  fill_uniform<S><<<1024, 256, 0, st>>>(T, (int64_t)te, 12, 0.0, 0.05);
+  fill_uniform<S><<<1024, 256, 0, st>>>(C1, (int64_t)(2 * nbatch * te), 13, -0.5, 0.5);
+  const size_t smem = smem_elems<S>() * sizeof(S);
+  cudaError_t e = cudaFuncSetAttribute(tsmqr_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(V, T, C1, C2, nb, ib);  // warm-up
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  for (int l = 0; l < launches; ++l) tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(V, T, C1, C2, nb, ib);
+  cudaEventRecord(e1, st);
+  e = cudaEventSynchronize(e1);
+  float ms = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return (int)e;
+  *sec = ms * 1e-3 / launches;
+  return 0;
+}
+
+// Step-2 timing of qr_factor at (m, n, nb, ib): reps runs, returns median and
+// min seconds. The matrix is regenerated on the device before every run.
+template <typename S>
+int time_factor(int64_t m, int64_t n, int nb, int ib, int reps, void* work, int64_t wbytes, cudaStream_t st,
+                double* med, double* mn) {
+  int64_t t_el = 0, sb = 0;
+  int rc = qr_workspace(m, n, nb, ib, sizeof(S) == 8 ? QR_PREC_F64 : QR_PREC_F32, &t_el, &sb);
+  if (rc) return rc;
+  const size_t a_bytes = ((size_t)m * n * sizeof(S) + 255) & ~(size_t)255;
+  const size_t t_bytes = ((size_t)t_el * sizeof(S) + 255) & ~(size_t)255;
+  if ((int64_t)(a_bytes + t_bytes + sb) > wbytes) return -7;
+  S* A = (S*)work;
+  S* T = (S*)((char*)work + a_bytes);
+  void* scr = (char*)work + a_bytes + t_bytes;
+  std::vector<double> ts;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int r = 0; r < reps + 1; ++r) {  // first run warms the schedule cache
+    fill_uniform<S><<<1184, 256, 0, st>>>(A, m * n, (uint64_t)(m * 31 + n), -0.5, 0.5);
+    cudaEventRecord(e0, st);
+    rc = sizeof(S) == 8 ? qr_factor_d(m, n, (double*)A, m, nb, ib, (double*)T, scr, sb, st)
+                        : qr_factor_s(m, n, (float*)A, m, nb, ib, (float*)T, scr, sb, st);
+    cudaEventRecord(e1, st);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { rc = (int)e; break; }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    int status = 0;
+    qr_status(scr, &status, st);
+    if (status) { rc = 1000 + status; break; }
+    if (r > 0) ts.push_back(ms * 1e-3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  std::sort(ts.begin(), ts.end());
+  *med = ts[ts.size() / 2];
+  if (ts.size() % 2 == 0) *med = 0.5 * (ts[ts.size() / 2 - 1] + ts[ts.size() / 2]);
+  *mn = ts.front();
+  return 0;
+}
+
+double qr_flops_d(int64_t m, int64_t n) { return 2.0 * m * (double)n * n - 2.0 * (double)n * n * n / 3.0; }
+
+// --- resumable JSONL log ------------------------------------------------------
+struct LogKey {
+  int kind;  // 1 = step 1, 2 = step 2
+  int64_t m, n;
+  int nb, ib;
+  bool operator<(const LogKey& o) const {
+    return std::tie(kind, m, n, nb, ib) < std::tie(o.kind, o.m, o.n, o.nb, o.ib);
+  }
+};
+
+void read_log(const char* path, std::map<LogKey, double>* seen) {
+  if (!path || !path[0]) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    int kind, nb, ib;
+    long long m, n;
+    double sec;
+    if (sscanf(line, "{\"kind\": %d, \"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"seconds\": %lf", &kind, &m,
+               &n, &nb, &ib, &sec) == 6)
+      (*seen)[LogKey{kind, m, n, nb, ib}] = sec;
+  }
+  fclose(f);
+}
+
+void append_log(const char* path, int kind, int64_t m, int64_t n, int nb, int ib, double sec, double smin,
+                int reps) {
+  if (!path || !path[0]) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"kind\": %d, \"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"seconds\": %.9g, \"min\": %.9g, "
+             "\"reps\": %d}\n",
+          kind, (long long)m, (long long)n, nb, ib, sec, smin, reps);
+  fclose(f);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib) {
+  std::lock_guard<std::mutex> lock(g_tmu);
+  const int p = elem_bytes == 4 ? 1 : 0;
+  if (lookup_entry(g_table[p], m, n, nb, ib) == 0) return 0;
+  if (p == 1 && lookup_entry(g_table[0], m, n, nb, ib) == 0) return 0;
+  *nb = 128;  // built-in default when nothing is loaded
+  *ib = 32;
+  return 0;
+}
+
+extern "C" {
+
+int qr_load_table(const char* path) {
+  if (!path) return -1;
+  int prec = 0;
+  std::vector<Entry> t;
+  if (!read_table(path, &prec, &t)) return -1;
+  std::lock_guard<std::mutex> lock(g_tmu);
+  g_table[prec] = t;
+  return 0;
+}
+
+int qr_clear_tables(void) {
+  std::lock_guard<std::mutex> lock(g_tmu);
+  g_table[0].clear();
+  g_table[1].clear();
+  return 0;
+}
+
+int qr_lookup(int64_t m, int64_t n, int prec, int* nb, int* ib) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
+  if (!nb) return -4;
+  if (!ib) return -5;
+  return qr_table_lookup(m, n, prec == QR_PREC_F32 ? 4 : 8, nb, ib);
+}
+
+int qr_tune_grid(int nb_lo, int nb_hi, int nb_step, int ib_min, int cap, int* nbs, int* ibs) {
+  if (nb_lo < 1 || nb_hi < nb_lo || nb_step < 1 || ib_min < 1) return -1;
+  auto g = grid_pairs(nb_lo, nb_hi, nb_step, ib_min);
+  if (nbs && ibs)
+    for (int i = 0; i < (int)g.size() && i < cap; ++i) {
+      nbs[i] = g[i].first;
+      ibs[i] = g[i].second;
+    }
+  return (int)g.size();
+}
+
+int qr_tune_preselect(int npairs, const int* nb, const int* ib, const double* perf, int heuristic, int max_sel,
+                      int nseg, int* sel_nb, int* sel_ib) {
+  if (npairs <= 0 || !nb || !ib || !perf) return -1;
+  if (heuristic < 0 || heuristic > 2) return -5;
+  std::map<int, std::pair<int, double>> best;  // Property 4.1
+  int lo = INT32_MAX, hi = 0;
+  for (int i = 0; i < npairs; ++i) {
+    lo = std::min(lo, nb[i]);
+    hi = std::max(hi, nb[i]);
+    auto it = best.find(nb[i]);
+    if (it == best.end() || perf[i] > it->second.second ||
+        (perf[i] == it->second.second && ib[i] < it->second.first))
+      best[nb[i]] = {ib[i], perf[i]};
+  }
+  std::vector<int> sel = select_nbs(best, heuristic, max_sel, nseg, lo, hi);
+  for (size_t i = 0; i < sel.size(); ++i) {
+    sel_nb[i] = sel[i];
+    sel_ib[i] = best[sel[i]].first;
+  }
+  return (int)sel.size();
+}
+
+int qr_tune_payg(int nsurv, const int* nb, const double* perf, int* keep) {
+  if (nsurv < 0 || (nsurv > 0 && (!nb || !perf || !keep))) return -1;
+  for (int a = 0; a < nsurv; ++a) {
+    keep[a] = 1;
+    for (int b = 0; b < nsurv; ++b)
+      if (nb[b] > nb[a] && perf[b] > perf[a]) keep[a] = 0;  // Property 5.1
+  }
+  return 0;
+}
+
+int64_t qr_tune_nearest(int64_t value, const int64_t* grid, int ngrid) {
+  if (ngrid <= 0 || !grid) return -1;
+  int64_t best = grid[0];
+  for (int i = 1; i < ngrid; ++i) {
+    const int64_t d = std::llabs(grid[i] - value), db = std::llabs(best - value);
+    if (d < db || (d == db && grid[i] < best)) best = grid[i];
+  }
+  return best;
+}
+
+int qr_step1_workspace(int nb, int prec, int64_t* bytes) {
+  if (nb < 8 || nb > 512) return -1;
+  if (!bytes) return -3;
+  *bytes = step1_bytes(nb, 2 * sm_count(), prec == QR_PREC_F32 ? 4 : 8);
+  return 0;
+}
+
+int qr_step1_time(int nb, int ib, int prec, int launches, double* seconds_per_launch, double* gflops,
+                  void* d_work, int64_t work_bytes, void* stream) {
+  if (nb < 8 || nb > 512) return -1;
+  if (ib < 1 || ib > nb || ib > 256) return -2;
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
+  if (launches < 1) return -4;
+  if (!seconds_per_launch) return -5;
+  const int nbatch = 2 * sm_count();
+  double s = 0;
+  const int rc = prec == QR_PREC_F64
+                     ? step1_time<double>(nb, ib, nbatch, launches, &s, d_work, work_bytes, (cudaStream_t)stream)
+                     : step1_time<float>(nb, ib, nbatch, launches, &s, d_work, work_bytes, (cudaStream_t)stream);
+  if (rc) return rc;
+  *seconds_per_launch = s;
+  if (gflops) *gflops = nbatch * 4.0 * nb * (double)nb * nb / s / 1e9;
+  return 0;
+}
+
+int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t* bytes) {
+  if (max_m < 1 || max_n < 1 || max_n > max_m) return -1;
+  if (!bytes) return -4;
+  const size_t esz = prec == QR_PREC_F32 ? 4 : 8;
+  int64_t best = step1_bytes(512, 2 * sm_count(), esz);
+  for (int nb = 64; nb <= 512; nb += 32) {
+    int64_t t_el = 0, sb = 0;
+    qr_workspace(max_m, max_n, nb, std::min(nb / 2, 256), prec, &t_el, &sb);
+    const int64_t need = (int64_t)(((size_t)max_m * max_n * esz + 255) & ~(size_t)255) +
+                         (int64_t)((t_el * esz + 255) & ~(size_t)255) + sb;
+    best = std::max(best, need);
+  }
+  *bytes = best;
+  return 0;
+}
+
+int qr_time_factor(int64_t m, int64_t n, int nb, int ib, int prec, int reps, double* median_s, double* min_s,
+                   void* d_work, int64_t work_bytes, void* stream) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (reps < 1) return -6;
+  if (!median_s || !min_s) return -7;
+  return prec == QR_PREC_F32 ? time_factor<float>(m, n, nb, ib, reps, d_work, work_bytes, (cudaStream_t)stream,
+                                                  median_s, min_s)
+                             : time_factor<double>(m, n, nb, ib, reps, d_work, work_bytes, (cudaStream_t)stream,
+                                                   median_s, min_s);
+}
+
+int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, int mode, int reps, int prec,
+            const char* table_path, const char* log_path, void* d_work, int64_t work_bytes, double* seconds_out,
+            void* stream) {
+  if (!ms || !ns || nshapes < 1) return -1;
+  if (heuristic < 0 || heuristic > 2) return -4;
+  if (mode < 0 || mode > 1) return -5;
+  if (reps < 1) return -6;
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -7;
+  if (!d_work) return -10;
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto t_start = std::chrono::steady_clock::now();
+  std::map<LogKey, double> seen;
+  read_log(log_path, &seen);
+  auto grid = grid_pairs(64, 512, 32, 8);
+  std::vector<std::pair<int, int>> cand;
+  double step1_s = 0;
+  if (mode == 1) {
+    cand = grid;  // exhaustive search over the grid
+  } else {
+    std::vector<int> nb(grid.size()), ib(grid.size());
+    std::vector<double> perf(grid.size());
+    for (size_t g = 0; g < grid.size(); ++g) {
+      nb[g] = grid[g].first;
+      ib[g] = grid[g].second;
+      double s = 0, gf = 0;
+      auto it = seen.find(LogKey{1, 0, 0, nb[g], ib[g]});
+      if (it != seen.end()) {
+        s = it->second;
+      } else {
+        const auto t0 = std::chrono::steady_clock::now();
+        int rc = qr_step1_time(nb[g], ib[g], prec, 50, &s, &gf, d_work, work_bytes, stream);
+        if (rc) return rc;
+        step1_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        append_log(log_path, 1, 0, 0, nb[g], ib[g], s, s, 50);
+      }
+      perf[g] = 2.0 * sm_count() * 4.0 * nb[g] * (double)nb[g] * nb[g] / s / 1e9;
+    }
+    std::vector<int> sn(grid.size()), si(grid.size());
+    const int k = qr_tune_preselect((int)grid.size(), nb.data(), ib.data(), perf.data(), heuristic, 8, 8, sn.data(),
+                                    si.data());
+    for (int i = 0; i < k; ++i) cand.push_back({sn[i], si[i]});
+  }
+  // Step 2: shapes in ascending order of n (then m), PSPAYG between orders
+  std::vector<int> order(nshapes);
+  for (int i = 0; i < nshapes; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return std::tie(ns[a], ms[a]) < std::tie(ns[b], ms[b]); });
+  std::vector<Entry> table;
+  std::vector<std::pair<int, int>> surv = cand;
+  double step2_s = 0;
+  int measured = 0;
+  for (int oi : order) {
+    const int64_t m = ms[oi], n = ns[oi];
+    std::vector<double> perf(surv.size(), 0.0);
+    for (size_t c = 0; c < surv.size(); ++c) {
+      double med = 0, mn = 0;
+      auto it = seen.find(LogKey{2, m, n, surv[c].first, surv[c].second});
+      if (it != seen.end()) {
+        med = it->second;
+      } else {
+        const auto t0 = std::chrono::steady_clock::now();
+        int rc = qr_time_factor(m, n, surv[c].first, surv[c].second, prec, reps, &med, &mn, d_work, work_bytes,
+                                stream);
+        if (rc) return rc;
+        step2_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        append_log(log_path, 2, m, n, surv[c].first, surv[c].second, med, mn, reps);
+        ++measured;
+      }
+      perf[c] = qr_flops_d(m, n) / med / 1e9;
+    }
+    size_t bi = 0;
+    for (size_t c = 1; c < surv.size(); ++c)
+      if (perf[c] > perf[bi] || (perf[c] == perf[bi] && surv[c].first < surv[bi].first)) bi = c;
+    table.push_back(Entry{m, n, surv[bi].first, surv[bi].second, perf[bi]});
+    if (mode == 0 && m == n) {  // prune as you go along the square orders
+      std::vector<int> nbv(surv.size()), keep(surv.size());
+      for (size_t c = 0; c < surv.size(); ++c) nbv[c] = surv[c].first;
+      qr_tune_payg((int)surv.size(), nbv.data(), perf.data(), keep.data());
+      std::vector<std::pair<int, int>> nx;
+      for (size_t c = 0; c < surv.size(); ++c)
+        if (keep[c]) nx.push_back(surv[c]);
+      surv = nx;
+    }
+  }
+  const double total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (seconds_out) {
+    seconds_out[0] = total;
+    seconds_out[1] = step1_s;
+    seconds_out[2] = step2_s;
+    seconds_out[3] = (double)measured;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    g_table[prec == QR_PREC_F32 ? 1 : 0] = table;
+  }
+  if (table_path && table_path[0]) {
+    char extra[512];
+    snprintf(extra, sizeof(extra),
+             "  \"heuristic\": %d,\n  \"mode\": \"%s\",\n  \"reps\": %d,\n  \"seconds\": %.3f,\n  \"step1_seconds\": "
+             "%.3f,\n  \"step2_seconds\": %.3f,\n",
+             heuristic, mode ? "exhaustive" : "pspayg", reps, total, step1_s, step2_s);
+    if (!write_table(table_path, prec == QR_PREC_F32 ? 1 : 0, table, extra)) return -8;
+  }
+  (void)st;
+  return 0;
+}
+
+}  // extern "C"

@@ -29,7 +29,9 @@ def to_dev(x):
 
 def _gpu_factor(q, A_np, nb, ib):
     A = to_dev(A_np)
-    f = q.qr_factor(A, nb, ib)
+    t_elems, _ = q.qr_workspace(A.shape[0], A.shape[1], nb, ib, A.dtype)
+    T = torch.zeros(max(t_elems, 1), dtype=A.dtype, device="cuda")  # unused slots stay zero
+    f = q.qr_factor(A, nb, ib, T=T)
     torch.cuda.synchronize()
     return f
 

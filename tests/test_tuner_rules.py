@@ -1,0 +1,117 @@
+"""The C++ tuner's decision rules (host-only entry points of libtileqr.so)
+against the Python oracle of the paper's rules, on random tables. CPU only:
+these calls make no GPU call."""
+import ctypes
+import json
+import os
+import random
+
+import pytest
+
+from oracle import tuning
+
+lib_mod = pytest.importorskip("paper_1102_5328_gb300._lib")
+
+
+@pytest.fixture(scope="module")
+def L():
+    return lib_mod.load()
+
+
+def _ia(xs):
+    return (ctypes.c_int * len(xs))(*xs)
+
+
+def _da(xs):
+    return (ctypes.c_double * len(xs))(*xs)
+
+
+def test_grid_matches(L):
+    n = L.qr_tune_grid(64, 512, 32, 8, 0, None, None)
+    nb = (ctypes.c_int * n)()
+    ib = (ctypes.c_int * n)()
+    assert L.qr_tune_grid(64, 512, 32, 8, n, nb, ib) == n
+    assert list(zip(nb, ib)) == tuning.grid_pairs()
+
+
+@pytest.mark.parametrize("heur", [0, 1, 2])
+@pytest.mark.parametrize("seed", range(15))
+def test_preselect_matches_oracle(L, heur, seed):
+    rng = random.Random(seed * 3 + heur)
+    pairs = tuning.grid_pairs()
+    # a rising, saturating kernel curve with noise, different per IB
+    perf = {(nb, ib): (1.0 - 2.0 ** (-nb / 150.0)) * (1.0 - 0.3 * ib / nb) + rng.uniform(-0.08, 0.08)
+            for nb, ib in pairs}
+    if seed % 3 == 0:  # sometimes a non-monotone curve
+        perf = {k: v + 0.2 * ((k[0] // 32) % 3 == 0) for k, v in perf.items()}
+    want = tuning.preselect(perf, heuristic=heur)
+    nb = [p[0] for p in pairs]
+    ib = [p[1] for p in pairs]
+    out_nb = (ctypes.c_int * 32)()
+    out_ib = (ctypes.c_int * 32)()
+    k = L.qr_tune_preselect(len(pairs), _ia(nb), _ia(ib), _da([perf[p] for p in pairs]), heur, 8, 8, out_nb, out_ib)
+    got = list(zip(out_nb[:k], out_ib[:k]))
+    assert got == want
+    if heur:
+        assert len(got) <= 8
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_payg_matches_oracle(L, seed):
+    rng = random.Random(seed)
+    nbs = sorted(rng.sample(range(64, 513, 32), rng.randint(1, 8)))
+    surv = [(nb, 8) for nb in nbs]
+    perf = {p: float(rng.randint(0, 5)) for p in surv}  # many ties
+    want = tuning.payg_prune(surv, perf)
+    keep = (ctypes.c_int * len(surv))()
+    assert L.qr_tune_payg(len(surv), _ia(nbs), _da([perf[p] for p in surv]), keep) == 0
+    assert [p for p, k in zip(surv, keep) if k] == want
+
+
+def test_nearest_matches_oracle(L):
+    grid = [1000, 2000, 4000, 6000, 8000, 10000]
+    g = (ctypes.c_int64 * len(grid))(*grid)
+    for v in list(range(0, 12001, 250)) + [1500, 3000, 5000, 7000, 9000]:
+        assert L.qr_tune_nearest(v, g, len(grid)) == tuning.nearest(v, grid)
+
+
+def test_table_roundtrip_and_lookup(L, tmp_path):
+    t = {"prec": "fp64", "entries": [
+        {"m": 1000, "n": 1000, "nb": 64, "ib": 16, "gflops": 100.0},
+        {"m": 2000, "n": 2000, "nb": 96, "ib": 32, "gflops": 300.0},
+        {"m": 10000, "n": 10000, "nb": 192, "ib": 32, "gflops": 900.0}]}
+    p = tmp_path / "t.json"
+    p.write_text(json.dumps(t, indent=2).replace('"m":', '"m":'))
+    # the library's reader wants its own flat one-line-per-entry format
+    lines = ['{', '  "prec": "fp64",', '  "entries": [']
+    for i, e in enumerate(t["entries"]):
+        lines.append('    {"m": %d, "n": %d, "nb": %d, "ib": %d, "gflops": %.4f}%s'
+                     % (e["m"], e["n"], e["nb"], e["ib"], e["gflops"], "," if i < 2 else ""))
+    lines += ['  ]', '}']
+    p.write_text("\n".join(lines))
+    assert L.qr_load_table(str(p).encode()) == 0
+    nb, ib = ctypes.c_int(), ctypes.c_int()
+    for n_req, expect in [(1800, 2000), (1400, 1000), (1500, 1000), (7000, 10000), (20000, 10000)]:
+        assert L.qr_lookup(n_req, n_req, 0, ctypes.byref(nb), ctypes.byref(ib)) == 0
+        e = [x for x in t["entries"] if x["n"] == tuning.nearest(n_req, [1000, 2000, 10000])][0]
+        assert e["n"] == expect
+        assert (nb.value, ib.value) == (e["nb"], e["ib"])
+    L.qr_clear_tables()
+    assert L.qr_lookup(5000, 5000, 0, ctypes.byref(nb), ctypes.byref(ib)) == 0
+    assert (nb.value, ib.value) == (128, 32)  # built-in default
+
+
+def test_every_declared_symbol_is_exported(L):
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = set()
+    for h in os.listdir(os.path.join(root, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(root, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:int|int64_t|double|void)\s+\**\s*(\w+)\s*\(", src, flags=re.M))
+    assert len(names) >= 10
+    for nm in sorted(names):
+        assert hasattr(L, nm), nm
+    declared = {s[0] for s in lib_mod.SIGNATURES}
+    assert names == declared, (names ^ declared)
