@@ -122,6 +122,67 @@ int qr_last_kernel_ms(float *ms);
  */
 int qr_peak_fp64(double *gflops, void *stream);
 
+/*
+ * Batched QR of many small matrices of uneven sizes (one persistent launch;
+ * batching is this library's extension of the paper's single-matrix QR).
+ * qr_batched_plan (host only): for count matrices of sizes m[b] x n[b]
+ *   (1 <= n <= m <= 65535) picks (nb, ib) per matrix from its size class
+ *   (qr_batched_set_class; force_nb > 0 overrides with (force_nb, force_ib)),
+ *   orders the matrices by decreasing flop count (largest first), and lays
+ *   out the T factors: t_offset_out[b] elements into one T array of
+ *   *t_total elements. All outputs are host arrays of count entries.
+ * qr_factor_batched_d / _s: every pointer argument is a DEVICE array of
+ *   count entries (d_A: device pointers to the column-major matrices, each
+ *   overwritten like qr_factor's output; d_lda; d_nb, d_ib, d_order,
+ *   d_t_offset as planned; d_T the T array). d_scratch: >= 256 bytes,
+ *   caller-owned (work counter + status word). Queues a memset and one
+ *   kernel on `stream`, so a call can be captured in a CUDA graph.
+ *   Each matrix is factored by one CTA in the flat-tree tile order of
+ *   Sec. 2.1 with its (nb, ib); qr_apply_qt_* with (m[b], n[b], nb=min(nb,m),
+ *   ib, T + t_offset[b]) applies its Q.
+ * qr_batched_set_class / qr_batched_clear_classes: the size-class table:
+ *   matrices with m <= m_hi (smallest such class) use (nb, ib); the default
+ *   is one tile per matrix with IB 16.
+ * qr_batched_status: synchronises `stream`, reads the status word
+ *   (QR_DEV_NONFINITE) of the last batched factorization using d_scratch.
+ */
+int qr_batched_plan(int count, const int *m, const int *n, int prec, int force_nb, int force_ib, int *nb_out,
+                    int *ib_out, int *order_out, int64_t *t_offset_out, int64_t *t_total);
+int qr_factor_batched_d(int count, const int *d_m, const int *d_n, double *const *d_A, const int *d_lda,
+                        double *d_T, const int64_t *d_t_offset, const int *d_nb, const int *d_ib,
+                        const int *d_order, void *d_scratch, void *stream);
+int qr_factor_batched_s(int count, const int *d_m, const int *d_n, float *const *d_A, const int *d_lda,
+                        float *d_T, const int64_t *d_t_offset, const int *d_nb, const int *d_ib,
+                        const int *d_order, void *d_scratch, void *stream);
+int qr_batched_set_class(int prec, int m_hi, int nb, int ib);
+int qr_batched_clear_classes(int prec);
+int qr_batched_status(const void *d_scratch, int *status, void *stream);
+
+/*
+ * qr_solve_ls_workspace / qr_solve_ls -- min ||A X - B||_F through the tile
+ * QR (least squares is the QR's use beyond the paper, which tunes the
+ * factorization only). A (m x n, m >= n, full rank), B (m x nrhs) and X
+ * (n x nrhs) are FP64 device arrays; A and B are not modified.
+ * prec = QR_PREC_F64: QR of an FP64 copy of A, X = R^{-1} (Q^T B)(0:n)
+ *   (max_iter > 0 adds FP64 refinement as below).
+ * prec = QR_PREC_F32: QR of an FP32 copy of A (FP64 kept in the panel's
+ *   Householder vector / tau generation), then refinement of the augmented
+ *   system [I A; A^T 0][r; x] = [b; 0] (Bjorck) with FP64 residuals
+ *   f = b - r - A x, g = -A^T r and FP64 accumulation of x and r; each
+ *   correction solves R^T h = g, d = Q^T f, R dx = d(0:n) - h,
+ *   dr = Q [h; d(n:m)] with the FP32 factors. Stops when every column has
+ *   ||dx|| <= tol ||x|| or after max_iter corrections.
+ * nb, ib: tile order / inner blocking of the factorization (0 = tuned table).
+ * info[3] (may be NULL): corrections taken (max over RHS groups), 1 if the
+ *   stopping test was met (1 also for a plain solve), device status bits.
+ * d_work (>= qr_solve_ls_workspace bytes) is caller-owned. Synchronises
+ * `stream` once per correction (stopping test) and at the end.
+ */
+int qr_solve_ls_workspace(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib, int64_t *bytes);
+int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t lda, const double *d_B, int64_t ldb,
+                double *d_X, int64_t ldx, int prec, int nb, int ib, int max_iter, double tol, int *info,
+                void *d_work, int64_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Empirical NB/IB autotuner (Secs. 4-5 of the paper).
  * ------------------------------------------------------------------------ */
@@ -157,7 +218,7 @@ int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t *bytes);
  * qr_load_table / qr_clear_tables / qr_lookup -- the decision table. A
  * request for an untuned shape uses the closest tuned one (Sec. 5.1: the
  * closest benchmarked configuration), distance |m - m_i| + |n - n_i|, ties
- * to the smaller tuned shape; with no table the built-in pair (128, 32).
+ * to the smaller tuned shape; with no table the built-in pair (128, 16).
  * prec selects the fp64 or fp32 table (fp32 falls back to fp64's).
  */
 int qr_load_table(const char *path);

@@ -127,6 +127,32 @@ def form_q(fact, stream=None):
     return qr_apply_qt(fact, Q, trans=False, stream=stream)
 
 
+def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, work=None, stream=None):
+    """min ||A X - B|| (A, B FP64, column-major CUDA tensors; unchanged).
+    Returns (X, info) with info = (corrections, converged, device status)."""
+    m, n = A.shape
+    nrhs = B.shape[1]
+    if A.dtype != torch.float64 or B.dtype != torch.float64:
+        raise TypeError("A and B must be float64")
+    if A.stride(0) != 1 or B.stride(0) != 1:
+        raise ValueError("A and B must be column-major")
+    if nb == 0:
+        nb, ib = qr_lookup(m, n, torch.float32 if prec == QR_PREC_F32 else torch.float64)
+    wb = ctypes.c_int64()
+    _lib.check(lib().qr_solve_ls_workspace(m, n, nrhs, prec, nb, ib, ctypes.byref(wb)), "qr_solve_ls_workspace")
+    if work is None or work.numel() < wb.value:
+        work = torch.empty(wb.value, dtype=torch.uint8, device=A.device)
+    X = colmajor_empty(n, nrhs, torch.float64, A.device)
+    info = (ctypes.c_int * 3)()
+    lda = A.stride(1) if n > 1 else m
+    ldb = B.stride(1) if nrhs > 1 else m
+    ldx = X.stride(1) if nrhs > 1 else n
+    _lib.check(lib().qr_solve_ls(m, n, nrhs, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(B.data_ptr()), ldb,
+                                 ctypes.c_void_p(X.data_ptr()), ldx, prec, nb, ib, max_iter, tol, info,
+                                 ctypes.c_void_p(work.data_ptr()), wb.value, _stream_ptr(stream)), "qr_solve_ls")
+    return X, tuple(info)
+
+
 def qr_status(scratch, stream=None):
     st = ctypes.c_int()
     _lib.check(lib().qr_status(ctypes.c_void_p(scratch.data_ptr()), ctypes.byref(st), _stream_ptr(stream)),
@@ -160,7 +186,9 @@ def qr_task_count(m, n, nb, ib):
 
 def qr_lookup(m, n, dtype=torch.float64):
     """(nb, ib) from the loaded tuning table (built-in default otherwise)."""
-    return 128, 32
+    nb, ib = ctypes.c_int(), ctypes.c_int()
+    _lib.check(lib().qr_lookup(m, n, _prec(dtype), ctypes.byref(nb), ctypes.byref(ib)), "qr_lookup")
+    return nb.value, ib.value
 
 
 def qr_flops(m, n):

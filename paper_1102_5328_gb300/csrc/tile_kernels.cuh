@@ -321,33 +321,41 @@ __device__ void build_t(const S* V, int ldv, bool v_smem, int nr, int ncol, cons
 // TS: pivot R(jj, jj) in Rs (w x w, upper), x = P(0:nr, jj), the update
 //     touches Rs(jj, c) and P(:, c).
 // Writes tau[0..w) and reports a non-finite norm through *bad.
+//
+// The norm, beta, tau and the scaling are always formed in FP64 (for the
+// FP32 working precision too: the Householder vector / tau generation is the
+// one place the mixed-precision path keeps FP64); the rank-1 updates run in S.
 template <typename S, bool TS>
 __device__ void panel_l2(S* P, int ldp, int nr, int w, S* Rs, int ldr, S* tau, S* red, int* bad) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* redd = reinterpret_cast<double*>(red);  // red holds >= 16 doubles
   for (int jj = 0; jj < w; ++jj) {
     const int x0 = TS ? 0 : jj + 1;
     S* col = P + (size_t)jj * ldp;
-    S s = S(0);
-    for (int r = x0 + threadIdx.x; r < nr; r += NTHREADS) s = fma(col[r], col[r], s);
-    const S xi2 = cta_sum(s, red);  // ends with a barrier
+    double s = 0.0;
+    for (int r = x0 + threadIdx.x; r < nr; r += NTHREADS) {
+      const double v = (double)col[r];
+      s = fma(v, v, s);
+    }
+    const double xi2 = cta_sum(s, redd);  // ends with a barrier
     S* piv = TS ? (Rs + jj + (size_t)jj * ldr) : (col + jj);
     if (threadIdx.x == 0) {
-      S tau_j = S(0), scal = S(0);
-      const S a = *piv;
+      double tau_j = 0.0, scal = 0.0;
+      const double a = (double)*piv;
       if (!isfinite(xi2) || !isfinite(a)) {
         atomicOr(bad, QR_DEV_NONFINITE);
-      } else if (xi2 != S(0)) {
-        const S nrm = sqrt(a * a + xi2);
-        const S beta = (a < S(0)) ? nrm : -nrm;
+      } else if (xi2 != 0.0) {
+        const double nrm = sqrt(a * a + xi2);
+        const double beta = (a < 0.0) ? nrm : -nrm;
         tau_j = (beta - a) / beta;
-        scal = S(1) / (a - beta);
-        *piv = beta;
+        scal = 1.0 / (a - beta);
+        *piv = (S)beta;
       }
-      tau[jj] = tau_j;
-      red[NTHREADS / 32 + 1] = scal;
+      tau[jj] = (S)tau_j;
+      redd[NTHREADS / 32 + 1] = scal;
     }
     __syncthreads();
-    const S scal = red[NTHREADS / 32 + 1];
+    const S scal = (S)redd[NTHREADS / 32 + 1];
     const S tj = tau[jj];
     for (int r = x0 + threadIdx.x; r < nr; r += NTHREADS) col[r] *= scal;
     __syncthreads();

@@ -338,7 +338,7 @@ int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib) {
   if (lookup_entry(g_table[p], m, n, nb, ib) == 0) return 0;
   if (p == 1 && lookup_entry(g_table[0], m, n, nb, ib) == 0) return 0;
   *nb = 128;  // built-in default when nothing is loaded
-  *ib = 32;
+  *ib = 16;
   return 0;
 }
 
@@ -485,7 +485,6 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
   if (reps < 1) return -6;
   if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -7;
   if (!d_work) return -10;
-  cudaStream_t st = (cudaStream_t)stream;
   const auto t_start = std::chrono::steady_clock::now();
   std::map<LogKey, double> seen;
   read_log(log_path, &seen);
@@ -578,7 +577,6 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
              heuristic, mode ? "exhaustive" : "pspayg", reps, total, step1_s, step2_s);
     if (!write_table(table_path, prec == QR_PREC_F32 ? 1 : 0, table, extra)) return -8;
   }
-  (void)st;
   return 0;
 }
 

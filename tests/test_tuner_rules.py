@@ -98,7 +98,7 @@ def test_table_roundtrip_and_lookup(L, tmp_path):
         assert (nb.value, ib.value) == (e["nb"], e["ib"])
     L.qr_clear_tables()
     assert L.qr_lookup(5000, 5000, 0, ctypes.byref(nb), ctypes.byref(ib)) == 0
-    assert (nb.value, ib.value) == (128, 32)  # built-in default
+    assert (nb.value, ib.value) == (128, 16)  # built-in default
 
 
 def test_every_declared_symbol_is_exported(L):
