@@ -173,8 +173,12 @@ int qr_batched_status(const void *d_scratch, int *status, void *stream);
  *   dr = Q [h; d(n:m)] with the FP32 factors. Stops when every column has
  *   ||dx|| <= tol ||x|| or after max_iter corrections.
  * nb, ib: tile order / inner blocking of the factorization (0 = tuned table).
- * info[3] (may be NULL): corrections taken (max over RHS groups), 1 if the
- *   stopping test was met (1 also for a plain solve), device status bits.
+ * info[3] (may be NULL): corrections taken (max over RHS groups); 1 if
+ *   every column met ||dx|| <= tol ||x|| (1 also for a plain solve), 2 if
+ *   the corrections stopped shrinking (no column's correction fell below
+ *   half the previous one, from the third correction on: the limiting
+ *   accuracy of FP64 residuals is reached), 0 if max_iter ran out first;
+ *   device status bits.
  * d_work (>= qr_solve_ls_workspace bytes) is caller-owned. Synchronises
  * `stream` once per correction (stopping test) and at the end.
  */
@@ -263,6 +267,30 @@ int qr_step1_time(int nb, int ib, int prec, int launches, double *seconds_per_la
  */
 int qr_time_factor(int64_t m, int64_t n, int nb, int ib, int prec, int reps, double *median_s, double *min_s,
                    void *d_work, int64_t work_bytes, void *stream);
+
+/*
+ * Learned cost model of the tuner (this library's addition; the paper tunes
+ * without a model, Secs. 1 and 3). A 4 -> 64 -> 64 -> 1 perceptron with ReLU
+ * hidden layers, FP32, mapping standardized (log m, log n, NB/512, IB/256)
+ * to log(seconds). d_params: QR_MLP_NPARAMS floats laid out W1 (64 x 4,
+ * row-major [out][in]), b1 (64), W2 (64 x 64), b2 (64), W3 (1 x 64), b3 (1).
+ * d_X: nsamp x 4 row-major; d_y: nsamp targets. Device pointers, async.
+ * qr_mlp_workspace: floats of scratch d_work needed by grad/train for nsamp.
+ * qr_mlp_forward: d_out[s] = prediction for sample s.
+ * qr_mlp_grad: d_grads (QR_MLP_NPARAMS + 1 floats) = gradient of
+ *   mean((yhat - y)^2) followed by the loss itself.
+ * qr_mlp_adam_step: one Adam update (beta1 0.9, beta2 0.999, eps 1e-8,
+ *   bias-corrected, step t >= 1) of d_params with moments d_m, d_v.
+ * qr_mlp_train: `steps` full-batch gradient + Adam steps (t = 1..steps).
+ */
+#define QR_MLP_NPARAMS 4545
+int qr_mlp_workspace(int nsamp, int64_t *floats);
+int qr_mlp_forward(int nsamp, const float *d_X, const float *d_params, float *d_out, void *stream);
+int qr_mlp_grad(int nsamp, const float *d_X, const float *d_y, const float *d_params, float *d_grads, float *d_work,
+                void *stream);
+int qr_mlp_adam_step(const float *d_grads, float *d_params, float *d_m, float *d_v, int t, float lr, void *stream);
+int qr_mlp_train(int nsamp, const float *d_X, const float *d_y, float *d_params, float *d_m, float *d_v, int steps,
+                 float lr, float *d_grads, float *d_work, void *stream);
 
 /* qr_task_count -- number of tasks of the factorization DAG (diagnostics). */
 int64_t qr_task_count(int64_t m, int64_t n, int nb, int ib);

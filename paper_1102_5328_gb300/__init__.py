@@ -153,6 +153,65 @@ def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, 
     return X, tuple(info)
 
 
+class BatchedPlan:
+    """Device-side descriptors of a batched QR (qr_batched_plan + upload)."""
+
+    def __init__(self, mats, force_nb=0, force_ib=0):
+        count = len(mats)
+        dtype = mats[0].dtype
+        dev = mats[0].device
+        ms = [int(a.shape[0]) for a in mats]
+        ns = [int(a.shape[1]) for a in mats]
+        I = ctypes.c_int * count
+        nb, ib, order = I(), I(), I()
+        toff = (ctypes.c_int64 * count)()
+        ttot = ctypes.c_int64()
+        _lib.check(lib().qr_batched_plan(count, I(*ms), I(*ns), _prec(dtype), force_nb, force_ib, nb, ib, order, toff,
+                                         ctypes.byref(ttot)), "qr_batched_plan")
+        self.count, self.dtype = count, dtype
+        self.m = torch.tensor(ms, dtype=torch.int32, device=dev)
+        self.n = torch.tensor(ns, dtype=torch.int32, device=dev)
+        self.lda = torch.tensor([a.stride(1) if a.shape[1] > 1 else a.shape[0] for a in mats], dtype=torch.int32,
+                                device=dev)
+        self.ptrs = torch.tensor([a.data_ptr() for a in mats], dtype=torch.int64, device=dev)
+        self.nb = torch.tensor(list(nb), dtype=torch.int32, device=dev)
+        self.ib = torch.tensor(list(ib), dtype=torch.int32, device=dev)
+        self.order = torch.tensor(list(order), dtype=torch.int32, device=dev)
+        self.toff = torch.tensor(list(toff), dtype=torch.int64, device=dev)
+        self.T = torch.zeros(ttot.value, dtype=dtype, device=dev)
+        self.scratch = torch.zeros(256, dtype=torch.uint8, device=dev)
+        self.h_nb, self.h_ib, self.h_toff = list(nb), list(ib), list(toff)
+
+    def launch(self, stream=None):
+        f = lib().qr_factor_batched_d if self.dtype == torch.float64 else lib().qr_factor_batched_s
+        P = ctypes.c_void_p
+        _lib.check(f(self.count, P(self.m.data_ptr()), P(self.n.data_ptr()), P(self.ptrs.data_ptr()),
+                     P(self.lda.data_ptr()), P(self.T.data_ptr()), P(self.toff.data_ptr()), P(self.nb.data_ptr()),
+                     P(self.ib.data_ptr()), P(self.order.data_ptr()), P(self.scratch.data_ptr()),
+                     _stream_ptr(stream)), "qr_factor_batched")
+
+    def status(self, stream=None):
+        st = ctypes.c_int()
+        _lib.check(lib().qr_batched_status(ctypes.c_void_p(self.scratch.data_ptr()), ctypes.byref(st),
+                                           _stream_ptr(stream)), "qr_batched_status")
+        return st.value
+
+    def factorization(self, b, A):
+        """Factorization view of matrix b (for qr_apply_qt / form_q)."""
+        m, n = A.shape
+        nbe = min(self.h_nb[b], m)
+        T = self.T[self.h_toff[b]:]
+        return Factorization(A, T, None, nbe, self.h_ib[b])
+
+
+def qr_batched_set_class(dtype, m_hi, nb, ib):
+    _lib.check(lib().qr_batched_set_class(_prec(dtype), m_hi, nb, ib), "qr_batched_set_class")
+
+
+def qr_batched_clear_classes(dtype):
+    _lib.check(lib().qr_batched_clear_classes(_prec(dtype)), "qr_batched_clear_classes")
+
+
 def qr_status(scratch, stream=None):
     st = ctypes.c_int()
     _lib.check(lib().qr_status(ctypes.c_void_p(scratch.data_ptr()), ctypes.byref(st), _stream_ptr(stream)),

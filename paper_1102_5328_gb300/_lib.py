@@ -38,6 +38,11 @@ SIGNATURES = [
     ("qr_task_count", c_i64, [c_i64, c_i64, c_int, c_int]),
     ("qr_last_kernel_ms", c_int, [ctypes.POINTER(ctypes.c_float)]),
     ("qr_load_table", c_int, [ctypes.c_char_p]),
+    ("qr_mlp_workspace", c_int, [c_int, ctypes.POINTER(c_i64)]),
+    ("qr_mlp_forward", c_int, [c_int, c_vp, c_vp, c_vp, c_vp]),
+    ("qr_mlp_grad", c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    ("qr_mlp_adam_step", c_int, [c_vp, c_vp, c_vp, c_vp, c_int, ctypes.c_float, c_vp]),
+    ("qr_mlp_train", c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_int, ctypes.c_float, c_vp, c_vp, c_vp]),
     ("qr_clear_tables", c_int, []),
     ("qr_lookup", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     ("qr_tune_grid", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),

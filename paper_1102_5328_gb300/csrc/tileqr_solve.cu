@@ -349,7 +349,7 @@ int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, cons
   cudaError_t e;
   if ((e = cudaMemsetAsync(x, 0, (size_t)n * nk * 8, st)) != cudaSuccess) return (int)e;
   if ((e = cudaMemsetAsync(r, 0, (size_t)m * nk * 8, st)) != cudaSuccess) return (int)e;
-  std::vector<double> hsq(2 * nk);
+  std::vector<double> hsq(2 * nk), prev(nk, 0.0);
   int it = 0, conv = 0;
   const int maxit = std::max(1, max_iter);
   for (; it < maxit && !conv;) {
@@ -380,16 +380,27 @@ int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, cons
     if (max_iter <= 0) break;  // plain solve: one pass, no refinement test
     if ((e = cudaMemcpyAsync(hsq.data(), sq, 2 * nk * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return (int)e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return (int)e;
-    conv = 1;
-    for (int k = 0; k < nk; ++k)
-      if (std::sqrt(hsq[2 * k]) > tol * std::sqrt(hsq[2 * k + 1])) conv = 0;
+    // stop when every column meets ||dx|| <= tol ||x|| (conv = 1), or when
+    // no column's correction shrank by half any more: the refinement has
+    // reached the accuracy its residual precision allows (conv = 2)
+    bool met = true, stalled = it >= 3;
+    for (int k = 0; k < nk; ++k) {
+      const double dxn = std::sqrt(hsq[2 * k]);
+      if (dxn > tol * std::sqrt(hsq[2 * k + 1])) met = false;
+      if (dxn <= 0.5 * prev[k]) stalled = false;  // this column still converges
+      prev[k] = dxn;
+    }
+    conv = met ? 1 : (stalled ? 2 : 0);
   }
   for (int k = 0; k < nk; ++k)
     if ((e = cudaMemcpyAsync(X + (size_t)k * ldx, x + (size_t)k * n, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) !=
         cudaSuccess)
       return (int)e;
   *iters = std::max(*iters, it);
-  if (!conv && max_iter > 0) *converged = 0;
+  if (max_iter > 0) {
+    if (!conv) *converged = 0;
+    else if (conv == 2 && *converged == 1) *converged = 2;
+  }
   return 0;
 }
 

@@ -41,7 +41,7 @@ def test_consistent_system(q):
         X, info = q.qr_solve_ls(to_dev(A), to_dev(B), prec=prec, nb=64, ib=16, max_iter=it)
         err = fwd_err(X.cpu().numpy(), x0).max()
         assert err < 1e3 * U * np.linalg.cond(A), (prec, err)
-        assert info[1] == 1 and info[2] == 0
+        assert info[1] in (1, 2) and info[2] == 0
 
 
 @pytest.mark.parametrize("m,n,kappa,nb,ib", [(600, 200, 1e5, 64, 16), (1024, 512, 1e6, 128, 32),
@@ -56,16 +56,25 @@ def test_mixed_matches_fp64_forward_error(q, m, n, kappa, nb, ib):
     Xmx, infomx = q.qr_solve_ls(to_dev(A), to_dev(B), prec=q.QR_PREC_F32, nb=nb, ib=ib, max_iter=50)
     e64 = fwd_err(X64.cpu().numpy(), Xref)
     emx = fwd_err(Xmx.cpu().numpy(), Xref)
-    assert infomx[1] == 1, infomx
+    assert infomx[1] in (1, 2), infomx  # tolerance met, or limiting accuracy reached
     assert np.all(emx <= 2 * e64 + 1e3 * U * kappa), (emx, e64)
     # FP64 path: within the LS perturbation bound kappa u + kappa^2 u tan(theta)
     assert np.all(e64 <= 50 * n * U * kappa * (1 + kappa)), e64
 
 
-def test_normal_equations_residual(q):
-    A, B = inputs.ls_problem(2048, 512, 4, kappa=1e6, seed=5)
-    X, info = q.qr_solve_ls(to_dev(A), to_dev(B), prec=q.QR_PREC_F32, nb=128, ib=32, max_iter=50)
-    X = X.cpu().numpy()
+def _normal_eq(A, B, X):
     R = B - A @ X
-    ne = np.linalg.norm(A.T @ R, axis=0) / (np.linalg.norm(A, 2) * np.linalg.norm(R, axis=0))
-    assert np.all(ne < 1e-12), ne
+    return np.linalg.norm(A.T @ R, axis=0) / (np.linalg.norm(A, 2) * np.linalg.norm(R, axis=0))
+
+
+def test_normal_equations_residual(q):
+    """||A^T r|| / (||A|| ||r||) of the mixed solution is as small as that of
+    the oracle's reference solution, up to the fp64 evaluation noise of the
+    check itself (of order kappa u)."""
+    kappa = 1e6
+    A, B = inputs.ls_problem(2048, 512, 4, kappa=kappa, seed=5)
+    X, info = q.qr_solve_ls(to_dev(A), to_dev(B), prec=q.QR_PREC_F32, nb=128, ib=32, max_iter=50)
+    Xref, _ = oracle.ls_refine(A, B, maxit=30)
+    ne = _normal_eq(A, B, X.cpu().numpy())
+    ne_ref = _normal_eq(A, B, Xref)
+    assert np.all(ne <= 4 * ne_ref + 10 * kappa * U), (ne, ne_ref)
