@@ -98,6 +98,31 @@ int qr_apply_qt_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64_t 
                   const float *d_T, float *d_C, int64_t ldc, int trans, void *stream);
 
 /*
+ * qr_factor_d_noalloc -- qr_factor_d for callers that cannot allocate device
+ * memory: code running where cudaMalloc is not allowed or not wanted, such
+ * as a plug-in handed pointers by a host application that owns every
+ * allocation, or a real-time loop that must not allocate. It takes no
+ * scratch buffer and calls no allocation routine; the paper has no
+ * counterpart (it is a convenience of this library).
+ * Its scratch is a fixed device array of QR_NOALLOC_SCRATCH_BYTES bytes
+ * compiled into the library; every GPU that loads the library holds it until
+ * the process exits. Problems whose scratch (as qr_workspace would report)
+ * exceeds that size are rejected with -1 before anything is queued (for
+ * example 1024 x 1024 with nb = 64 fits; 4096 x 4096 does not).
+ * Arguments as qr_factor_d; d_A and d_T are the caller's input/output.
+ * d_status (device int, may be NULL) receives the QR_DEV_* bits of this call.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array: calls that
+ * overlap on the GPU (concurrent streams, several host threads) race and
+ * corrupt each other -- serialise them. Each call clears the status word,
+ * ticket and counters it needs; tasks run in the DAG's program order.
+ */
+#define QR_NOALLOC_SCRATCH_BYTES (16u << 20)
+int qr_factor_d_noalloc(int64_t m, int64_t n, double *d_A, int64_t lda, int nb, int ib, double *d_T,
+                        int *d_status, void *stream);
+
+/*
  * qr_status -- synchronises `stream`, then copies the device status word of
  * the factorization that last used d_scratch into *status (QR_DEV_* bits).
  */

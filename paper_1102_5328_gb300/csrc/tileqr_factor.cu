@@ -428,6 +428,97 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant (qr_factor_d_noalloc). Its scratch -- status word,
+// ticket, progress counters, task list and tile-layout copy of A -- lives in
+// this fixed device array instead of a caller buffer. Host code must not pass
+// the symbol itself to a kernel (on the host it names a stand-in, not device
+// memory); the device address comes from cudaGetSymbolAddress, once per
+// device, on the first call made with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QR_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Program (k-major) order of the flat-tree DAG, written by the device: one
+// thread per elimination step, each computing its own offset.
+__global__ void gen_program_order(int MT, int NT, int S, uint64_t* tasks) {
+  const int K = min(MT, NT);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  int64_t off = 0;
+  for (int kk = 0; kk < k; ++kk)
+    off += 1 + (int64_t)(NT - kk - 1) * S + (int64_t)(MT - kk - 1) * (1 + (int64_t)(NT - kk - 1) * S);
+  tasks[off++] = encode_task(TASK_GEQRT, 0, k, k, k);
+  for (int j = k + 1; j < NT; ++j)
+    for (int s = 0; s < S; ++s) tasks[off++] = encode_task(TASK_UNMQR, s, k, j, k);
+  for (int i = k + 1; i < MT; ++i) {
+    tasks[off++] = encode_task(TASK_TSQRT, 0, i, k, k);
+    for (int j = k + 1; j < NT; ++j)
+      for (int s = 0; s < S; ++s) tasks[off++] = encode_task(TASK_TSMQR, s, i, j, k);
+  }
+}
+
+__global__ void copy_status(const DevCtl* ctl, int* out) { *out = ctl->status; }
+
+int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, int* d_status,
+                        void* stream) {
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (!A && m * n > 0) return -3;
+  if (lda < std::max<int64_t>(m, 1)) return -4;
+  if (nb == 0) {
+    if (qr_table_lookup(m, n, 8, &nb, &ib) != 0) return -5;
+  }
+  if (nb < 8 || nb > 512) return -5;
+  if (ib < 1 || ib > nb || ib > 256) return -6;
+  if (m == 0 || n == 0) return 0;
+  if (!T) return -7;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const Layout L = make_layout(m, n, nb, ib, sizeof(double));
+  if (L.bytes > (size_t)QR_NOALLOC_SCRATCH_BYTES) return -1;  // too large for the fixed scratch
+  if (L.MT > 65535 || L.NT > 65535) return -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev < 0 || dev >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return (int)e;
+    g_noalloc_ptr[dev] = p;
+  }
+  char* base = (char*)g_noalloc_ptr[dev];
+  DevCtl* ctl = (DevCtl*)base;
+  unsigned* cnt = (unsigned*)(base + L.off_cnt);
+  uint64_t* dtasks = (uint64_t*)(base + L.off_tasks);
+  double* W = (double*)(base + L.off_tiles);
+  const int K = std::min(L.MT, L.NT);
+  gen_program_order<<<(K + 127) / 128, 128, 0, st>>>(L.MT, L.NT, L.S, dtasks);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  // the status word, ticket and every progress counter start at zero
+  const int64_t nzero = (int64_t)(L.off_cnt / sizeof(unsigned)) + (int64_t)L.MT * L.NT * L.S;
+  cm_to_tiles<double><<<1184, 256, 0, st>>>(A, lda, m, n, W, nb, L.MT, L.NT, (unsigned*)base, nzero);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  int grid = 0;
+  int rc = persistent_grid<double>(&grid);
+  if (rc) return rc;
+  FactorArgs<double> fa;
+  fa.W = W; fa.T = T; fa.m = m; fa.n = n; fa.NB = nb; fa.IB = ib; fa.MT = L.MT; fa.NT = L.NT; fa.S_ = L.S;
+  fa.tasks = dtasks; fa.ntasks = L.ntasks; fa.cnt = cnt; fa.ctl = ctl;
+  fa.timeout_ns = (uint64_t)g_wait_timeout_us * 1000ull;
+  persistent_qr<double><<<grid, NTHREADS, smem_elems<double>() * sizeof(double), st>>>(fa);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  tiles_to_cm<double><<<1184, 256, 0, st>>>(W, A, lda, m, n, nb, L.MT);
+  if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  if (d_status) {
+    copy_status<<<1, 1, 0, st>>>(ctl, d_status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  }
+  return 0;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -465,6 +556,11 @@ int qr_factor_d(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, do
 int qr_factor_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, float* T, void* scratch,
                 int64_t scratch_bytes, void* stream) {
   return factor_impl<float>(m, n, A, lda, nb, ib, T, scratch, scratch_bytes, stream);
+}
+
+int qr_factor_d_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, int* d_status,
+                        void* stream) {
+  return factor_noalloc_impl(m, n, A, lda, nb, ib, T, d_status, stream);
 }
 
 int qr_status(const void* scratch, int* status, void* stream) {
