@@ -159,6 +159,110 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """Batched uneven QR: 4096 matrices, m ~ U{32..512}, n ~ U{16..m}, N(0,1),
+    one persistent launch captured in a CUDA graph with the input restore,
+    replayed; GFLOP/s = sum of credited flops / median replay time."""
+    import torch
+
+    import paper_1102_5328_gb300 as q
+    from paper_1102_5328_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    out = {}
+    ms, ns = inputs.batch_shapes(args.count, seed=4)
+    mats = inputs.batch_matrices(ms, ns, seed=5)
+    total_flops = float(sum(q.qr_flops(int(m), int(n)) for m, n in zip(ms, ns)))
+    sizes = [int(m) * int(n) for m, n in zip(ms, ns)]
+    offs = np.concatenate([[0], np.cumsum([(sz + 31) // 32 * 32 for sz in sizes])])
+    flat_np = np.zeros(int(offs[-1]))
+    for a, o in zip(mats, offs[:-1]):
+        flat_np[int(o):int(o) + a.size] = np.ascontiguousarray(a.T).reshape(-1)
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        # all matrices in one buffer: the graph restores them with one copy
+        src_flat = torch.from_numpy(flat_np).to(dt).cuda()
+        work_flat = src_flat.clone()
+        work = [work_flat[int(o):int(o) + int(m) * int(n)].view(int(n), int(m)).t()
+                for o, m, n in zip(offs[:-1], ms, ns)]
+        plan = q.BatchedPlan(work, args.nb, args.ib)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.launch(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            work_flat.copy_(src_flat)
+            plan.launch(stream=torch.cuda.current_stream())
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(args.steps, 20)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        med = statistics.median(times)
+        out[name] = {"median_ms": med, "gflops": total_flops / (med * 1e-3) / 1e9, "replays": len(times),
+                     "status": plan.status()}
+    line = {"workload": "batched uneven QR, %d matrices, m~U{32..512}, n~U{16..m}, N(0,1)" % args.count,
+            "metric": "GFLOP/s (sum of 2mn^2-2n^3/3 per replay)", "unit": "GFLOP/s",
+            "credited_gflop_per_batch": total_flops / 1e9, "results": out,
+            "note": "each replay restores the inputs (device copy) and runs one persistent launch"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ls(args):
+    """Least squares, A = U diag(sigma) V^T (16384 x 4096, kappa 1e6), 8 RHS:
+    plain FP64 QR solve vs FP32 factorization + FP64 augmented refinement;
+    forward error against the oracle's doubled-precision refined solution."""
+    import torch
+
+    import paper_1102_5328_gb300 as q
+    from paper_1102_5328_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    m, n, k = args.ls_m, args.ls_n, 8
+    A_np, B_np = inputs.ls_problem(m, n, k, kappa=1e6, seed=5)
+    A = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()
+    B = torch.from_numpy(np.ascontiguousarray(B_np.T)).cuda().t()
+    res = {}
+    for name, prec, it in (("fp64", q.QR_PREC_F64, 0), ("mixed_fp32_ir", q.QR_PREC_F32, 50)):
+        nb, ib = (args.nb, args.ib) if args.nb else q.qr_lookup(m, n, torch.float64)
+        X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it)  # warm-up
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(args.steps, 3)):
+            t0 = time.perf_counter()
+            X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        res[name] = {"median_s": statistics.median(ts), "info": list(info), "nb": nb, "ib": ib,
+                     "X": X.cpu().numpy()}
+    line = {"workload": "least squares %dx%d, kappa 1e6, %d RHS N(0,1)" % (m, n, k), "metric": "seconds per solve"}
+    if not args.no_cpu:
+        import oracle
+        Xref, its = oracle.ls_refine(A_np, B_np, maxit=30)
+        for name in res:
+            X = res[name].pop("X")
+            fe = np.linalg.norm(X - Xref, axis=0) / np.linalg.norm(Xref, axis=0)
+            res[name]["forward_error_max"] = float(fe.max())
+            res[name]["forward_error"] = [float(v) for v in fe]
+        line["oracle_refinement_iterations"] = its
+    else:
+        for name in res:
+            res[name].pop("X")
+    line["results"] = res
+    line["speedup_mixed_over_fp64"] = res["fp64"]["median_s"] / res["mixed_fp32_ir"]["median_s"]
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,9 +274,18 @@ def main():
     ap.add_argument("--ib", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--workload", default="qr", choices=["qr", "batched", "ls"],
+                    help="qr: the headline line; batched / ls: the extension workloads (own JSON lines)")
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--ls-m", type=int, default=16384)
+    ap.add_argument("--ls-n", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "ls":
+        return run_ls(args)
 
     import torch
     import torch.distributed as dist

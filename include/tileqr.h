@@ -278,6 +278,8 @@ int64_t qr_tune_nearest(int64_t value, const int64_t *grid, int ngrid);
  * for one (nb, ib): `launches` back-to-back launches of a batch of
  * 2 x (SM count) independent TSMQR tile tasks (same data every launch:
  * "No Flush"), timed with CUDA events on `stream`; synchronous.
+ * launches <= 0 picks the count from one timed launch: enough launches for
+ * about 30 ms, at least 3 and at most the paper's 50.
  * *seconds_per_launch, and *gflops (may be NULL) = batch x 4 NB^3 / time.
  */
 int qr_step1_workspace(int nb, int prec, int64_t *bytes);
@@ -286,8 +288,10 @@ int qr_step1_time(int nb, int ib, int prec, int launches, double *seconds_per_la
 
 /*
  * qr_time_factor -- the Step-2 measurement: qr_factor at (m, n, nb, ib) on a
- * device-generated uniform[-0.5, 0.5) matrix, reps timed runs after one
- * warm-up (CUDA events around each call), median and minimum seconds.
+ * device-generated uniform[-0.5, 0.5) matrix regenerated before each run,
+ * reps timed runs (CUDA events around each call; the host task order is
+ * built beforehand, and problems of at most 4e6 elements get one untimed
+ * warm-up run), median and minimum seconds.
  * d_work must hold A (m x n), T and the factorization scratch.
  */
 int qr_time_factor(int64_t m, int64_t n, int nb, int ib, int prec, int reps, double *median_s, double *min_s,

@@ -204,17 +204,33 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       }
       // --- phase B: W <- T_l^T W; TS: Ctop rows -= W
       {
+        // T_l from global memory is staged in shared memory first (the
+        // partial-sum buffer is free now), so the triangular products below
+        // do not wait on an L2 round trip per element
+        const S* Tb = T + (size_t)l0 * ldt;  // element (q, p) at Tb[q + p * ldtb]
+        int ldtb = ldt;
+        bool tsm = t_smem;
+        if (!t_smem && ib * ib <= PART_CAP) {
+          for (int idx = tid; idx < ib * ib; idx += NTHREADS) {
+            const int p = idx / ib, q = idx - (idx / ib) * ib;
+            sm.part[idx] = (q <= p) ? ldg(Tb + q + (size_t)p * ldt) : S(0);
+          }
+          __syncthreads();
+          Tb = sm.part;
+          ldtb = ib;
+          tsm = true;
+        }
         S wq[16];
         int no = 0;
         for (int o = tid; o < ib * cw && no < 16; o += NTHREADS, ++no) {
           const int p = o / cw, cc = o - (o / cw) * cw;
           S s = S(0);
           if (TR) {
-            const S* tcol = T + (size_t)(l0 + p) * ldt;
-            for (int q = 0; q <= p; ++q) s = fma(ldx(tcol + q, t_smem), sm.w[q * cw + cc], s);
+            const S* tcol = Tb + (size_t)p * ldtb;
+            for (int q = 0; q <= p; ++q) s = fma(ldx(tcol + q, tsm), sm.w[q * cw + cc], s);
           } else {
-            const S* trow = T + p + (size_t)l0 * ldt;
-            for (int q = p; q < ib; ++q) s = fma(ldx(trow + (size_t)q * ldt, t_smem), sm.w[q * cw + cc], s);
+            const S* trow = Tb + p;
+            for (int q = p; q < ib; ++q) s = fma(ldx(trow + (size_t)q * ldtb, tsm), sm.w[q * cw + cc], s);
           }
           wq[no] = s;
         }
@@ -300,6 +316,23 @@ __device__ void build_t(const S* V, int ldv, bool v_smem, int nr, int ncol, cons
   }
   for (int p = threadIdx.x; p < ncol; p += NTHREADS) stx(Tout + p + (size_t)p * ldt, tau[p], t_smem);
   __syncthreads();
+  if (ncol <= 32) {
+    // one warp, lane q owns row q of T; no CTA-wide barrier per column
+    if (wid == 0) {
+      for (int p = 1; p < ncol; ++p) {
+        const S tp = tau[p];
+        S t = S(0);
+        if (lane < p && tp != S(0))
+          for (int s2 = lane; s2 < p; ++s2)
+            t = fma(ldx(Tout + lane + (size_t)s2 * ldt, t_smem), ldx(Tout + s2 + (size_t)p * ldt, t_smem), t);
+        __syncwarp();
+        if (lane < p) stx(Tout + lane + (size_t)p * ldt, -tp * t, t_smem);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int p = 1; p < ncol; ++p) {
     const S tp = tau[p];
     S t = S(0);
@@ -328,37 +361,37 @@ __device__ void build_t(const S* V, int ldv, bool v_smem, int nr, int ncol, cons
 template <typename S, bool TS>
 __device__ void panel_l2(S* P, int ldp, int nr, int w, S* Rs, int ldr, S* tau, S* red, int* bad) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double* redd = reinterpret_cast<double*>(red);  // red holds >= 16 doubles
   for (int jj = 0; jj < w; ++jj) {
     const int x0 = TS ? 0 : jj + 1;
     S* col = P + (size_t)jj * ldp;
-    double s = 0.0;
-    for (int r = x0 + threadIdx.x; r < nr; r += NTHREADS) {
-      const double v = (double)col[r];
-      s = fma(v, v, s);
-    }
-    const double xi2 = cta_sum(s, redd);  // ends with a barrier
-    S* piv = TS ? (Rs + jj + (size_t)jj * ldr) : (col + jj);
-    if (threadIdx.x == 0) {
-      double tau_j = 0.0, scal = 0.0;
-      const double a = (double)*piv;
-      if (!isfinite(xi2) || !isfinite(a)) {
-        atomicOr(bad, QR_DEV_NONFINITE);
-      } else if (xi2 != 0.0) {
-        const double nrm = sqrt(a * a + xi2);
-        const double beta = (a < 0.0) ? nrm : -nrm;
-        tau_j = (beta - a) / beta;
-        scal = 1.0 / (a - beta);
-        *piv = (S)beta;
+    // warp 0 forms the reflector: norm, beta, tau, scaling of x
+    if (wid == 0) {
+      double s = 0.0;
+      for (int r = x0 + lane; r < nr; r += 32) {
+        const double v = (double)col[r];
+        s = fma(v, v, s);
       }
-      tau[jj] = (S)tau_j;
-      redd[NTHREADS / 32 + 1] = scal;
+      s = warp_sum(s);
+      S* piv = TS ? (Rs + jj + (size_t)jj * ldr) : (col + jj);
+      double tau_j = 0.0, scal = 0.0;
+      if (lane == 0) {
+        const double a = (double)*piv;
+        if (!isfinite(s) || !isfinite(a)) {
+          atomicOr(bad, QR_DEV_NONFINITE);
+        } else if (s != 0.0) {
+          const double nrm = sqrt(a * a + s);
+          const double beta = (a < 0.0) ? nrm : -nrm;
+          tau_j = (beta - a) / beta;
+          scal = 1.0 / (a - beta);
+          *piv = (S)beta;
+        }
+        tau[jj] = (S)tau_j;
+      }
+      const S sc = (S)__shfl_sync(0xffffffffu, scal, 0);
+      for (int r = x0 + lane; r < nr; r += 32) col[r] *= sc;
     }
     __syncthreads();
-    const S scal = (S)redd[NTHREADS / 32 + 1];
     const S tj = tau[jj];
-    for (int r = x0 + threadIdx.x; r < nr; r += NTHREADS) col[r] *= scal;
-    __syncthreads();
     if (tj != S(0)) {
       for (int cc = jj + 1 + wid; cc < w; cc += NTHREADS / 32) {
         S* pc = P + (size_t)cc * ldp;

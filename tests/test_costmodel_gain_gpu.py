@@ -1,0 +1,62 @@
+"""What the learned cost model adds to the paper's method, on a synthetic
+timing surface (deterministic, no timing noise): the MLP, trained by the
+library's own kernels on the training shapes, picks better (NB, IB) pairs on
+held-out shapes than the paper's closest-tuned-shape interpolation (Sec. 5.1).
+
+The surface: kernel efficiency grows with NB and loses IB/NB, parallelism
+shrinks with the tile count, so the best NB moves with the shape."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import tuning
+from paper_1102_5328_gb300 import inputs
+
+
+def flops(m, n):
+    return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+def synth_time(m, n, nb, ib):
+    eff = (1 - np.exp(-nb / 90.0)) * (1 - 0.25 * ib / nb)
+    tiles = np.ceil(m / nb) * np.ceil(n / nb)
+    par = 1 - np.exp(-tiles / 300.0)
+    return flops(m, n) / (1e12 * eff * par)
+
+
+@pytest.fixture(scope="module")
+def cm():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1102_5328_gb300 import costmodel
+    return costmodel
+
+
+def test_model_beats_nearest_interpolation(cm):
+    pairs = tuning.grid_pairs()
+    train = [(1000, 1000), (2000, 2000), (4000, 4000), (8000, 8000), (20000, 500), (100000, 256), (50000, 2000)]
+    held = [(3000, 3000), (6000, 6000), (30000, 1000)]
+    X = [(m, n, nb, ib) for (m, n) in train for (nb, ib) in pairs]
+    F = cm.features(*zip(*X))
+    y = np.log([synth_time(*x) for x in X])
+    model = cm.CostModel(inputs.mlp_init(2024))
+    Z = model.standardize(F, fit=True)
+    ym = y.mean()
+    loss = model.train(Z, y - ym, steps=3000, lr=3e-3)
+    assert loss < 0.01
+    table = {s: min(pairs, key=lambda p: synth_time(*s, *p)) for s in train}
+    reg_near, reg_model = [], []
+    for s in held:
+        P = {p: flops(*s) / synth_time(*s, *p) for p in pairs}
+        best = max(P, key=P.get)
+        near = table[min(table, key=lambda t: (abs(t[0] - s[0]) + abs(t[1] - s[1]), t[0] + t[1]))]
+        pred = model.forward(model.standardize(cm.features([s[0]] * len(pairs), [s[1]] * len(pairs),
+                                                           [p[0] for p in pairs], [p[1] for p in pairs])))
+        top3 = [pairs[i] for i in np.argsort(pred)[:3]]
+        pick = max(top3, key=P.get)  # the measurement decides among the model's top 3
+        reg_near.append(1 - P[near] / P[best])
+        reg_model.append(1 - P[pick] / P[best])
+    assert np.mean(reg_model) < np.mean(reg_near), (reg_model, reg_near)
+    assert np.mean(reg_model) < 0.03, reg_model
