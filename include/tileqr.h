@@ -98,6 +98,27 @@ int qr_apply_qt_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64_t 
                   const float *d_T, float *d_C, int64_t ldc, int trans, void *stream);
 
 /*
+ * qr_apply_workspace / qr_apply_qt_ws_d / qr_apply_qt_ws_s -- the same
+ * product as qr_apply_qt_* (trans = 1: C <- Q^T C, 0: C <- Q C), scheduled
+ * like the factorization's updates: C takes the place of a trailing tile
+ * column, UNMQR on its row block k and TSMQR on its row blocks (k, i) run
+ * as tasks of a persistent kernel that waits on per-row-block counters, so
+ * few right-hand sides still spread over many SMs (successive elimination
+ * steps proceed as a wavefront). Column chunks of at most 64 columns are
+ * separate tasks. d_scratch (bytes from qr_apply_workspace for the same m, n,
+ * nrhs, nb) is caller-owned; the task list is uploaded and the counters
+ * cleared on every call. Arguments otherwise as qr_apply_qt_*; -12: no
+ * scratch, -13: scratch too small.
+ */
+int qr_apply_workspace(int64_t m, int64_t n, int64_t nrhs, int nb, int64_t *bytes);
+int qr_apply_qt_ws_d(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t lda, int nb, int ib,
+                     const double *d_T, double *d_C, int64_t ldc, int trans, void *d_scratch, int64_t scratch_bytes,
+                     void *stream);
+int qr_apply_qt_ws_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64_t lda, int nb, int ib,
+                     const float *d_T, float *d_C, int64_t ldc, int trans, void *d_scratch, int64_t scratch_bytes,
+                     void *stream);
+
+/*
  * qr_factor_d_noalloc -- qr_factor_d for callers that cannot allocate device
  * memory: code running where cudaMalloc is not allowed or not wanted, such
  * as a plug-in handed pointers by a host application that owns every

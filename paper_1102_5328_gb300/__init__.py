@@ -11,6 +11,8 @@ Matrices are column-major: a torch tensor ``A`` of shape (m, n) with
 ``A.stride() == (1, lda)`` (see :func:`colmajor`).
 """
 import ctypes
+import json
+import os
 
 import torch
 
@@ -28,8 +30,29 @@ QR_OPT_DROP_TASK = 5
 QR_OPT_RECORD_EVENTS = 6
 
 
+_TUNED_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")
+_tables_loaded = False
+
+
 def lib():
-    return _lib.load()
+    """The loaded C library; on first use also installs the committed tuning
+    results for this GPU (decision table of qr_tune, batched size classes)."""
+    global _tables_loaded
+    L = _lib.load()
+    if not _tables_loaded:
+        _tables_loaded = True
+        for name in ("gb300_fp64.json", "gb300_fp32.json"):
+            path = os.path.join(_TUNED_DIR, name)
+            if os.path.exists(path):
+                L.qr_load_table(path.encode())
+        path = os.path.join(_TUNED_DIR, "gb300_batched_classes.json")
+        if os.path.exists(path):
+            with open(path) as f:
+                cls = json.load(f)
+            for prec_name, prec in (("f64", QR_PREC_F64), ("f32", QR_PREC_F32)):
+                for m_hi, v in cls.get(prec_name, {}).items():
+                    L.qr_batched_set_class(prec, int(m_hi), int(v["best"][0]), int(v["best"][1]))
+    return L
 
 
 def _stream_ptr(stream=None):
@@ -102,8 +125,10 @@ def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None):
     return Factorization(A, T, scratch, nb, ib)
 
 
-def qr_apply_qt(fact, C, trans=True, stream=None):
-    """C <- Q^T C (trans) or Q C, in place, with the factors of qr_factor."""
+def qr_apply_qt(fact, C, trans=True, stream=None, parallel=True):
+    """C <- Q^T C (trans) or Q C, in place, with the factors of qr_factor.
+    parallel=True uses the dependency-ordered persistent kernel
+    (qr_apply_qt_ws_*), False the column-chunk kernel (qr_apply_qt_*)."""
     if C.stride(0) != 1:
         raise ValueError("C must be column-major (use colmajor())")
     if C.dtype != fact.A.dtype:
@@ -113,18 +138,27 @@ def qr_apply_qt(fact, C, trans=True, stream=None):
     ldc = C.stride(1) if nrhs > 1 else m
     f = lib().qr_apply_qt_d if C.dtype == torch.float64 else lib().qr_apply_qt_s
     lda = fact.A.stride(1) if n > 1 else m
+    if parallel:
+        wb = ctypes.c_int64()
+        _lib.check(lib().qr_apply_workspace(m, n, nrhs, fact.nb, ctypes.byref(wb)), "qr_apply_workspace")
+        ws = torch.empty(wb.value, dtype=torch.uint8, device=C.device)
+        f = lib().qr_apply_qt_ws_d if C.dtype == torch.float64 else lib().qr_apply_qt_ws_s
+        _lib.check(f(m, n, nrhs, ctypes.c_void_p(fact.A.data_ptr()), lda, fact.nb, fact.ib,
+                     ctypes.c_void_p(fact.T.data_ptr()), ctypes.c_void_p(C.data_ptr()), ldc, 1 if trans else 0,
+                     ctypes.c_void_p(ws.data_ptr()), wb.value, _stream_ptr(stream)), "qr_apply_qt_ws")
+        return C
     _lib.check(f(m, n, nrhs, ctypes.c_void_p(fact.A.data_ptr()), lda, fact.nb, fact.ib,
                  ctypes.c_void_p(fact.T.data_ptr()), ctypes.c_void_p(C.data_ptr()), ldc, 1 if trans else 0,
                  _stream_ptr(stream)), "qr_apply_qt")
     return C
 
 
-def form_q(fact, stream=None):
+def form_q(fact, stream=None, parallel=True):
     """Explicit thin Q (m x n) = Q [I; 0], on the GPU."""
     Q = colmajor_empty(fact.m, fact.n, fact.A.dtype, fact.A.device)
     Q.zero_()
     Q.diagonal().fill_(1)
-    return qr_apply_qt(fact, Q, trans=False, stream=stream)
+    return qr_apply_qt(fact, Q, trans=False, stream=stream, parallel=parallel)
 
 
 def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, work=None, stream=None):

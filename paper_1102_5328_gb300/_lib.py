@@ -23,6 +23,11 @@ SIGNATURES = [
     ("qr_apply_qt_d", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp]),
     ("qr_apply_qt_s", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp]),
     ("qr_status", c_int, [c_vp, ctypes.POINTER(c_int), c_vp]),
+    ("qr_apply_workspace", c_int, [c_i64, c_i64, c_i64, c_int, ctypes.POINTER(c_i64)]),
+    ("qr_apply_qt_ws_d", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp, c_i64,
+                                 c_vp]),
+    ("qr_apply_qt_ws_s", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp, c_i64,
+                                 c_vp]),
     ("qr_batched_plan", c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int, c_int, c_int,
                                 ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                 ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),

@@ -132,6 +132,14 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
   const int cwmax = min(NTHREADS / G, W_CAP / ibmax);
   const int nchunks = (c1 - c0 + cwmax - 1) / cwmax;
   const int per = (c1 - c0 + nchunks - 1) / nchunks;
+  const int nblk = (lend - lstart + IB - 1) / IB;
+  // TS blocks whose reflectors fit one staging buffer are double-buffered:
+  // while the CTA updates C with block b, cp.async copies block b+1's
+  // reflectors into the other buffer (vs and part swap the roles of V stage
+  // and partial-sum buffer) and each thread holds part of b+1's T in a
+  // register. 16-byte copies need an even leading dimension and an aligned V.
+  const bool can_pipe = TS && ((ldv & 1) == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0) &&
+                        sizeof(S) == 8;
   for (int cs = c0; cs < c1; cs += per) {
     const int cw = min(per, c1 - cs);
     const int g = tid / cw, c = tid - (tid / cw) * cw;
@@ -142,7 +150,8 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       const int r = g * RPT + rr;
       creg[rr] = (act && r < rows) ? ldg(C + r + (size_t)(cs + c) * ldc) : S(0);
     }
-    const int nblk = (lend - lstart + IB - 1) / IB;
+    int vcur = 0;           // which buffer holds the current block's V (0: vs, 1: part)
+    bool staged = false;    // current block's V (and T in ts) already in place
     for (int bi = 0; bi < nblk; ++bi) {
       const int l0 = lstart + (TR ? bi : nblk - 1 - bi) * IB;
       const int ib = min(IB, lend - l0);
@@ -151,100 +160,134 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       const int glo = rlo / RPT;
       const int rlo_al = glo * RPT;
       const int nr = G * RPT - rlo_al;  // staged rows, zero-padded past `rows`
-      int PB = VS_CAP / nr;
+      S* vbuf = vcur ? sm.part : sm.vs;
+      S* pbuf = vcur ? sm.vs : sm.part;
+      const int vcap = vcur ? PART_CAP : VS_CAP;
+      int PB = vcap / nr;
       if (PB > ib) PB = ib;
       if (PB < 1) PB = 1;
       const bool myrows = act && g >= glo;
+      // T_l in shared memory (ts) unless it is there already
+      const bool t_in_ts = !t_smem && ib * ib <= TS_CAP;
       // --- phase A: W = Vfull^T Cstack, V staged PB reflectors at a time
       for (int pp0 = 0; pp0 < ib; pp0 += PB) {
         const int pb = min(PB, ib - pp0);
-        __syncthreads();
-        for (int idx = tid; idx < pb * nr; idx += NTHREADS) {
-          const int p = idx / nr, rl = idx - (idx / nr) * nr;
-          const int r = rl + rlo_al, pc = l0 + pp0 + p;
-          S v = S(0);
-          if (r < rows) {
-            if (TS) {
-              v = ldg(V + r + (size_t)pc * ldv);
-            } else {
-              v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
+        if (!staged) {
+          __syncthreads();
+          for (int idx = tid; idx < pb * nr; idx += NTHREADS) {
+            const int p = idx / nr, rl = idx - (idx / nr) * nr;
+            const int r = rl + rlo_al, pc = l0 + pp0 + p;
+            S v = S(0);
+            if (r < rows) {
+              if (TS) {
+                v = ldg(V + r + (size_t)pc * ldv);
+              } else {
+                v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
+              }
             }
+            vbuf[p * nr + rl] = v;
           }
-          sm.vs[rl * PB + p] = v;
+          if (pp0 == 0 && t_in_ts)
+            for (int idx = tid; idx < ib * ib; idx += NTHREADS) {
+              const int p = idx / ib, q = idx - (idx / ib) * ib;
+              sm.ts[idx] = (q <= p) ? ldg(T + q + (size_t)(l0 + p) * ldt) : S(0);
+            }
+          __syncthreads();
         }
-        __syncthreads();
         for (int pg0 = 0; pg0 < pb; pg0 += PG) {
           const int pgc = min(PG, pb - pg0);
           if (myrows) {
             S acc[PG];
 #pragma unroll
             for (int q = 0; q < PG; ++q) acc[q] = S(0);
-            const S* vrow = sm.vs + (size_t)(g * RPT - rlo_al) * PB + pg0;
+            const S* vrow = vbuf + (size_t)pg0 * nr + (g * RPT - rlo_al);
 #pragma unroll
             for (int rr = 0; rr < RPT; ++rr) {
               const S cv = creg[rr];
 #pragma unroll
               for (int q = 0; q < PG; ++q)
-                if (q < pgc) acc[q] = fma(vrow[rr * PB + q], cv, acc[q]);
+                if (q < pgc) acc[q] = fma(vrow[q * nr + rr], cv, acc[q]);
             }
 #pragma unroll
             for (int q = 0; q < PG; ++q)
-              if (q < pgc) sm.part[(q * G + g) * cw + c] = acc[q];
+              if (q < pgc) pbuf[(q * G + g) * cw + c] = acc[q];
           }
           __syncthreads();
           for (int o = tid; o < pgc * cw; o += NTHREADS) {
             const int q = o / cw, cc = o - (o / cw) * cw;
             const int p = pp0 + pg0 + q;
             S s = TS ? ldg(Ctop + (l0 + p) + (size_t)(cs + cc) * ldct) : S(0);
-            for (int gg = glo; gg < G; ++gg) s += sm.part[(q * G + gg) * cw + cc];
+            for (int gg = glo; gg < G; ++gg) s += pbuf[(q * G + gg) * cw + cc];
             sm.w[p * cw + cc] = s;
           }
           __syncthreads();
         }
       }
-      // --- phase B: W <- T_l^T W; TS: Ctop rows -= W
+      // --- phase B: W <- T_l^T W (Q^T) or T_l W (Q); TS: Ctop rows -= W
       {
-        // T_l from global memory is staged in shared memory first (the
-        // partial-sum buffer is free now), so the triangular products below
-        // do not wait on an L2 round trip per element
-        const S* Tb = T + (size_t)l0 * ldt;  // element (q, p) at Tb[q + p * ldtb]
-        int ldtb = ldt;
-        bool tsm = t_smem;
-        if (!t_smem && ib * ib <= PART_CAP) {
-          for (int idx = tid; idx < ib * ib; idx += NTHREADS) {
-            const int p = idx / ib, q = idx - (idx / ib) * ib;
-            sm.part[idx] = (q <= p) ? ldg(Tb + q + (size_t)p * ldt) : S(0);
-          }
-          __syncthreads();
-          Tb = sm.part;
-          ldtb = ib;
-          tsm = true;
-        }
+        const S* Tb = t_in_ts ? sm.ts : T + (size_t)l0 * ldt;  // (q, p) at Tb[q + p * ldtb]
+        const int ldtb = t_in_ts ? ib : ldt;
+        const bool tsm = t_in_ts || t_smem;
+        // ib * cw <= W_CAP = 16 * NTHREADS: at most 16 outputs per thread,
+        // held in registers (compile-time indices) until every read of W is done
         S wq[16];
-        int no = 0;
-        for (int o = tid; o < ib * cw && no < 16; o += NTHREADS, ++no) {
-          const int p = o / cw, cc = o - (o / cw) * cw;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int o = tid + u * NTHREADS;
           S s = S(0);
-          if (TR) {
-            const S* tcol = Tb + (size_t)p * ldtb;
-            for (int q = 0; q <= p; ++q) s = fma(ldx(tcol + q, tsm), sm.w[q * cw + cc], s);
-          } else {
-            const S* trow = Tb + p;
-            for (int q = p; q < ib; ++q) s = fma(ldx(trow + (size_t)q * ldtb, tsm), sm.w[q * cw + cc], s);
+          if (o < ib * cw) {
+            const int p = o / cw, cc = o - (o / cw) * cw;
+            if (TR) {
+              const S* tcol = Tb + (size_t)p * ldtb;
+              for (int q = 0; q <= p; ++q) s = fma(ldx(tcol + q, tsm), sm.w[q * cw + cc], s);
+            } else {
+              const S* trow = Tb + p;
+              for (int q = p; q < ib; ++q) s = fma(ldx(trow + (size_t)q * ldtb, tsm), sm.w[q * cw + cc], s);
+            }
           }
-          wq[no] = s;
+          wq[u] = s;
         }
         __syncthreads();
-        no = 0;
-        for (int o = tid; o < ib * cw && no < 16; o += NTHREADS, ++no) {
-          const int p = o / cw, cc = o - (o / cw) * cw;
-          sm.w[p * cw + cc] = wq[no];
-          if (TS) {
-            S* pt = Ctop + (l0 + p) + (size_t)(cs + cc) * ldct;
-            stg(pt, ldg(pt) - wq[no]);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int o = tid + u * NTHREADS;
+          if (o < ib * cw) {
+            const int p = o / cw, cc = o - (o / cw) * cw;
+            sm.w[p * cw + cc] = wq[u];
+            if (TS) {
+              S* pt = Ctop + (l0 + p) + (size_t)(cs + cc) * ldct;
+              stg(pt, ldg(pt) - wq[u]);
+            }
           }
         }
         __syncthreads();
+      }
+      // --- prefetch of the next block (TS, single stage in the other buffer)
+      bool pre = false;
+      S tpre = S(0);
+      int ibn = 0, l0n = 0;
+      if (can_pipe && bi + 1 < nblk && PB == ib) {
+        l0n = lstart + (TR ? bi + 1 : nblk - 2 - bi) * IB;
+        ibn = min(IB, lend - l0n);
+        const int ocap = vcur ? VS_CAP : PART_CAP;
+        if (ibn * nr <= ocap && (t_smem || ibn * ibn <= NTHREADS)) {  // one T element per thread
+          pre = true;
+          S* nbuf = vcur ? sm.vs : sm.part;
+          const int half = nr / 2;
+          for (int idx = tid; idx < ibn * half; idx += NTHREADS) {
+            const int p = idx / half, r = 2 * (idx - (idx / half) * half);
+            const int valid = r < rows ? min(2, rows - r) * (int)sizeof(S) : 0;
+            const S* src = V + (valid ? r + (size_t)(l0n + p) * ldv : 0);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(nbuf + p * nr + r);
+            const size_t gsrc = __cvta_generic_to_global(src);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gsrc), "r"(valid) : "memory");
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          if (!t_smem && tid < ibn * ibn) {
+            const int p = tid / ibn, q = tid - (tid / ibn) * ibn;
+            tpre = (q <= p) ? ldg(T + q + (size_t)(l0n + p) * ldt) : S(0);
+          }
+        }
       }
       // --- phase C: Cstack -= Vfull W (restage V if it did not fit at once)
       for (int pp0 = 0; pp0 < ib; pp0 += PB) {
@@ -262,20 +305,31 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
                 v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
               }
             }
-            sm.vs[rl * PB + p] = v;
+            vbuf[p * nr + rl] = v;
           }
           __syncthreads();
         }
         if (myrows) {
-          const S* vrow = sm.vs + (size_t)(g * RPT - rlo_al) * PB;
+          const S* vrow = vbuf + (g * RPT - rlo_al);
           for (int p = 0; p < pb; ++p) {
             const S wv = sm.w[(pp0 + p) * cw + c];
+            const S* vp = vrow + (size_t)p * nr;
 #pragma unroll
-            for (int rr = 0; rr < RPT; ++rr) creg[rr] = fma(-vrow[rr * PB + p], wv, creg[rr]);
+            for (int rr = 0; rr < RPT; ++rr) creg[rr] = fma(-vp[rr], wv, creg[rr]);
           }
         }
       }
-      __syncthreads();
+      if (pre) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();  // every thread's phase C reads of ts/vbuf are done
+        if (!t_smem && tid < ibn * ibn) sm.ts[tid] = tpre;
+        vcur ^= 1;
+        staged = true;
+        __syncthreads();
+      } else {
+        staged = false;
+        __syncthreads();
+      }
     }
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {

@@ -21,6 +21,7 @@
 #include <tuple>
 #include <vector>
 
+#include "sched.cuh"
 #include "tile_kernels.cuh"
 #include "tileqr_internal.h"
 
@@ -193,46 +194,6 @@ __global__ void tiles_to_cm(const S* __restrict__ W, S* __restrict__ A, int64_t 
 
 // ---------------------------------------------------------------------------
 // Device: the persistent scheduler.
-struct DevCtl {
-  int status;
-  int abort;
-  unsigned ticket;
-};
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait until all counters c[0..cnt) reach v. Bounded by time and by
-// iterations; on expiry sets the timeout bit and the abort flag.
-__device__ bool wait_ge(const unsigned* c, int cnt, unsigned v, DevCtl* ctl, uint64_t timeout_ns) {
-  const uint64_t t0 = globaltimer();
-  const uint64_t max_iter = timeout_ns / 16 + 4096;
-  uint64_t iter = 0;
-  for (int q = 0; q < cnt; ++q) {
-    while (ld_acquire(c + q) < v) {
-      if (((volatile int*)&ctl->abort)[0]) return false;
-      if (++iter > max_iter || globaltimer() - t0 > timeout_ns) {
-        atomicOr(&ctl->status, QR_DEV_TIMEOUT);
-        atomicExch(&ctl->abort, 1);
-        return false;
-      }
-      __nanosleep(100);
-    }
-  }
-  return true;
-}
-
 template <typename S>
 struct FactorArgs {
   S* W;

@@ -243,7 +243,8 @@ __global__ void accumulate(int64_t rows, int nk, const S* v, int64_t ldv, const 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct SolveLayout {
-  size_t a, t, scr, bw, hw, tw, x, r, f, g, p, q, scale, sq, total;
+  size_t a, t, scr, ap, bw, hw, tw, x, r, f, g, p, q, scale, sq, total;
+  int64_t apbytes;
   int64_t t_el, sbytes;
   int nsplit, nrb, rpb;
   int64_t cps;
@@ -258,6 +259,8 @@ SolveLayout solve_layout(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, i
   L.a = off; off = al(off + (size_t)m * n * es);
   L.t = off; off = al(off + (size_t)L.t_el * es);
   L.scr = off; off = al(off + (size_t)L.sbytes);
+  qr_apply_workspace(m, n, std::min<int64_t>(nrhs, 8), nb, &L.apbytes);
+  L.ap = off; off = al(off + (size_t)L.apbytes);
   L.bw = off; off = al(off + (size_t)m * k8 * es);
   L.hw = off; off = al(off + (size_t)n * k8 * es);
   L.tw = off; off = al(off + (size_t)n * k8 * es);
@@ -310,17 +313,20 @@ int trsm(int64_t n, const S* R, int64_t ldr, S* X, int64_t ldx, int nk, int tran
   return e == cudaSuccess ? 0 : (int)e;
 }
 
+// Q^T / Q through the dependency-ordered persistent application (few
+// right-hand sides still use many SMs).
 template <typename S>
-int apply(int64_t m, int64_t n, int64_t nk, const S* A, int nb, int ib, const S* T, S* C, int trans, cudaStream_t st);
+int apply(int64_t m, int64_t n, int64_t nk, const S* A, int nb, int ib, const S* T, S* C, int trans, void* ws,
+          int64_t wsb, cudaStream_t st);
 template <>
-int apply<double>(int64_t m, int64_t n, int64_t nk, const double* A, int nb, int ib, const double* T, double* C, int trans,
-                  cudaStream_t st) {
-  return qr_apply_qt_d(m, n, nk, A, m, nb, ib, T, C, m, trans, st);
+int apply<double>(int64_t m, int64_t n, int64_t nk, const double* A, int nb, int ib, const double* T, double* C,
+                  int trans, void* ws, int64_t wsb, cudaStream_t st) {
+  return qr_apply_qt_ws_d(m, n, nk, A, m, nb, ib, T, C, m, trans, ws, wsb, st);
 }
 template <>
 int apply<float>(int64_t m, int64_t n, int64_t nk, const float* A, int nb, int ib, const float* T, float* C, int trans,
-                 cudaStream_t st) {
-  return qr_apply_qt_s(m, n, nk, A, m, nb, ib, T, C, m, trans, st);
+                 void* ws, int64_t wsb, cudaStream_t st) {
+  return qr_apply_qt_ws_s(m, n, nk, A, m, nb, ib, T, C, m, trans, ws, wsb, st);
 }
 
 // colmax wrote max|f| into scale[0..nk) and max|g| into scale[8..8+nk);
@@ -365,13 +371,13 @@ int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, cons
     // R^T h = g/s
     if ((rc = trsm<S>(n, Af, m, Hw, n, nk, 1, st))) return rc;
     // d = Q^T f/s
-    if ((rc = apply<S>(m, n, nk, Af, nb, ib, T, Bw, 1, st))) return rc;
+    if ((rc = apply<S>(m, n, nk, Af, nb, ib, T, Bw, 1, w + L.ap, L.apbytes, st))) return rc;
     // Tw = d(0:n) - h ; Bw(0:n) = h
     split_correction<S><<<grid_for(n * nk), TB, 0, st>>>(m, n, nk, Bw, Hw, Tw);
     // R dx = Tw
     if ((rc = trsm<S>(n, Af, m, Tw, n, nk, 0, st))) return rc;
     // dr = Q [h; d(n:m)]
-    if ((rc = apply<S>(m, n, nk, Af, nb, ib, T, Bw, 0, st))) return rc;
+    if ((rc = apply<S>(m, n, nk, Af, nb, ib, T, Bw, 0, w + L.ap, L.apbytes, st))) return rc;
     if ((e = cudaMemsetAsync(sq, 0, 2 * 8 * 8, st)) != cudaSuccess) return (int)e;
     accumulate<S><<<dim3(64, nk), TB, 0, st>>>(n, nk, Tw, n, scale, x, n, sq);
     accumulate<S><<<dim3(256, nk), TB, 0, st>>>(m, nk, Bw, m, scale, r, m, nullptr);

@@ -105,6 +105,14 @@ def test_apply_qt_is_transpose(q):
     assert np.abs(QtA[n:]).max() < 50 * n * U
     q.qr_apply_qt(f, C, trans=False)
     assert torch.allclose(C, C0, atol=100 * n * U, rtol=0)
+    # the column-chunk kernel and the dependency-ordered persistent kernel
+    # perform the same operations per column: identical results
+    for trans in (True, False):
+        C1 = to_dev(inputs.normal_matrix(m, 70, seed=3))
+        C2 = C1.clone().t().contiguous().t()
+        q.qr_apply_qt(f, C1, trans=trans, parallel=False)
+        q.qr_apply_qt(f, C2, trans=trans, parallel=True)
+        assert torch.equal(C1, C2)
 
 
 def test_deterministic_and_schedule_independent(q):
@@ -154,3 +162,23 @@ def test_invalid_arguments_rejected(q):
     assert lib.qr_factor_d(100, 50, ctypes.c_void_p(A.data_ptr()), 100, 600, 8, None, None, 0, None) == -5
     assert lib.qr_factor_d(100, 50, ctypes.c_void_p(A.data_ptr()), 100, 32, 33, None, None, 0, None) == -6
     assert lib.qr_factor_d(50, 100, ctypes.c_void_p(A.data_ptr()), 100, 32, 8, None, None, 0, None) == -2
+
+
+def test_double_buffered_staging_is_bitwise_neutral(q):
+    """The TS-mode update double-buffers its reflector staging only when the
+    reflector array has an even leading dimension; the arithmetic is the same
+    either way, so applying Q^T from a copy of the factors with an odd
+    leading dimension must give bitwise the same result."""
+    m, n = 400, 300
+    A = inputs.uniform_matrix(m, n, seed=21)
+    f = _gpu_factor(q, A, 64, 16)
+    A_odd_store = torch.zeros((n, m + 1), dtype=torch.float64, device="cuda")
+    A_odd = A_odd_store.t()[:m]  # column-major view, lda = m + 1 (odd)
+    A_odd.copy_(f.A)
+    f_odd = q.Factorization(A_odd, f.T, None, f.nb, f.ib)
+    for trans in (True, False):
+        C1 = to_dev(inputs.normal_matrix(m, 40, seed=8))
+        C2 = C1.clone().t().contiguous().t()
+        q.qr_apply_qt(f, C1, trans=trans)
+        q.qr_apply_qt(f_odd, C2, trans=trans)
+        assert torch.equal(C1, C2)
