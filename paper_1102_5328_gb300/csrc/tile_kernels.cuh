@@ -137,9 +137,10 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
   // while the CTA updates C with block b, cp.async copies block b+1's
   // reflectors into the other buffer (vs and part swap the roles of V stage
   // and partial-sum buffer) and each thread holds part of b+1's T in a
-  // register. 16-byte copies need an even leading dimension and an aligned V.
-  const bool can_pipe = TS && ((ldv & 1) == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0) &&
-                        sizeof(S) == 8;
+  // register. 16-byte copies need a leading dimension that is a multiple of
+  // 16 bytes and a 16-byte aligned V.
+  constexpr int EPC = 16 / sizeof(S);  // elements per 16-byte copy
+  const bool can_pipe = TS && (ldv % EPC == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0);
   for (int cs = c0; cs < c1; cs += per) {
     const int cw = min(per, c1 - cs);
     const int g = tid / cw, c = tid - (tid / cw) * cw;
@@ -273,10 +274,10 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         if (ibn * nr <= ocap && (t_smem || ibn * ibn <= NTHREADS)) {  // one T element per thread
           pre = true;
           S* nbuf = vcur ? sm.vs : sm.part;
-          const int half = nr / 2;
+          const int half = nr / EPC;  // nr is a multiple of 32, so of EPC
           for (int idx = tid; idx < ibn * half; idx += NTHREADS) {
-            const int p = idx / half, r = 2 * (idx - (idx / half) * half);
-            const int valid = r < rows ? min(2, rows - r) * (int)sizeof(S) : 0;
+            const int p = idx / half, r = EPC * (idx - (idx / half) * half);
+            const int valid = r < rows ? min(EPC, rows - r) * (int)sizeof(S) : 0;
             const S* src = V + (valid ? r + (size_t)(l0n + p) * ldv : 0);
             const unsigned dst = (unsigned)__cvta_generic_to_shared(nbuf + p * nr + r);
             const size_t gsrc = __cvta_generic_to_global(src);
