@@ -50,6 +50,7 @@ extern "C" {
 #define QR_OPT_GRID_LIMIT      4 /* cap on persistent CTAs (0 = all SMs); 1 = sequential */
 #define QR_OPT_DROP_TASK       5 /* test hook: omit this ticket from the task list (-1 = off) */
 #define QR_OPT_RECORD_EVENTS   6 /* 1: bracket each persistent kernel with CUDA events on its stream */
+#define QR_OPT_ORDER           7 /* flat-tree ticket order: 0 earliest start time, 1 list schedule (default) */
 
 /*
  * qr_workspace -- sizes of the caller-owned buffers of qr_factor_*.
@@ -117,6 +118,41 @@ int qr_apply_qt_ws_d(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int6
 int qr_apply_qt_ws_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64_t lda, int nb, int ib,
                      const float *d_T, float *d_C, int64_t ldc, int trans, void *d_scratch, int64_t scratch_bytes,
                      void *stream);
+
+/*
+ * Tile QR with p domains per panel (the paper's third tunable for
+ * tall-skinny matrices, communication-avoiding QR, Sec. 6).
+ * qr_workspace_p / qr_factor_p_d / qr_factor_p_s: as qr_workspace /
+ *   qr_factor_*, with p >= 1 domains: at each step the tile rows below the
+ *   panel are cut into p contiguous ranges, each eliminated by its own flat
+ *   tree (GEQRT on its first tile, TSQRT down the range, UNMQR/TSMQR
+ *   updates), and the p triangles are merged by a binary tree of
+ *   triangle-on-triangle steps (TTQRT, with TTMQR updates). p = 1 is the
+ *   flat tree of qr_factor_* (same arithmetic). A ragged last tile row is
+ *   never a domain head. Output: R in the upper triangle of d_A; below it the
+ *   reflectors; a domain head's tile keeps its GEQRT reflectors below the
+ *   diagonal and, once its triangle is merged away, the TTQRT reflectors in
+ *   its upper triangle. d_T holds t_elems = 2 x MT x NT x IB x NB elements
+ *   (GEQRT/TSQRT factors, then TTQRT factors). Scratch as qr_workspace_p
+ *   reports (it includes the explicit task list). -7: p out of [1, 4096].
+ * qr_apply_workspace_p / qr_apply_qt_p_d / qr_apply_qt_p_s: C <- Q^T C
+ *   (trans = 1) or Q C for the factors of qr_factor_p_* with the same
+ *   (m, n, nb, ib, p); a persistent kernel over C's row blocks with explicit
+ *   dependencies. -8: bad p; -13: no scratch; -14: scratch too small.
+ */
+int qr_workspace_p(int64_t m, int64_t n, int nb, int ib, int p, int prec, int64_t *t_elems,
+                   int64_t *scratch_bytes);
+int qr_factor_p_d(int64_t m, int64_t n, double *d_A, int64_t lda, int nb, int ib, int p, double *d_T,
+                  void *d_scratch, int64_t scratch_bytes, void *stream);
+int qr_factor_p_s(int64_t m, int64_t n, float *d_A, int64_t lda, int nb, int ib, int p, float *d_T,
+                  void *d_scratch, int64_t scratch_bytes, void *stream);
+int qr_apply_workspace_p(int64_t m, int64_t n, int64_t nrhs, int nb, int p, int64_t *bytes);
+int qr_apply_qt_p_d(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t lda, int nb, int ib, int p,
+                    const double *d_T, double *d_C, int64_t ldc, int trans, void *d_scratch, int64_t scratch_bytes,
+                    void *stream);
+int qr_apply_qt_p_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64_t lda, int nb, int ib, int p,
+                    const float *d_T, float *d_C, int64_t ldc, int trans, void *d_scratch, int64_t scratch_bytes,
+                    void *stream);
 
 /*
  * qr_factor_d_noalloc -- qr_factor_d for callers that cannot allocate device
@@ -219,6 +255,8 @@ int qr_batched_status(const void *d_scratch, int *status, void *stream);
  *   dr = Q [h; d(n:m)] with the FP32 factors. Stops when every column has
  *   ||dx|| <= tol ||x|| or after max_iter corrections.
  * nb, ib: tile order / inner blocking of the factorization (0 = tuned table).
+ * p: panel domains of the factorization (qr_factor_p_*); 0 picks
+ *   ceil(MT / NT) tile-row ranges per panel, at most 32 (1 = flat tree).
  * info[3] (may be NULL): corrections taken (max over RHS groups); 1 if
  *   every column met ||dx|| <= tol ||x|| (1 also for a plain solve), 2 if
  *   the corrections stopped shrinking (no column's correction fell below
@@ -228,9 +266,9 @@ int qr_batched_status(const void *d_scratch, int *status, void *stream);
  * d_work (>= qr_solve_ls_workspace bytes) is caller-owned. Synchronises
  * `stream` once per correction (stopping test) and at the end.
  */
-int qr_solve_ls_workspace(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib, int64_t *bytes);
+int qr_solve_ls_workspace(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib, int p, int64_t *bytes);
 int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t lda, const double *d_B, int64_t ldb,
-                double *d_X, int64_t ldx, int prec, int nb, int ib, int max_iter, double tol, int *info,
+                double *d_X, int64_t ldx, int prec, int nb, int ib, int p, int max_iter, double tol, int *info,
                 void *d_work, int64_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------------

@@ -28,6 +28,7 @@ QR_OPT_SPLIT = 3
 QR_OPT_GRID_LIMIT = 4
 QR_OPT_DROP_TASK = 5
 QR_OPT_RECORD_EVENTS = 6
+QR_OPT_ORDER = 7
 
 
 _TUNED_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")
@@ -91,10 +92,11 @@ def qr_workspace(m, n, nb, ib, dtype=torch.float64):
 
 class Factorization:
     """Result of qr_factor: A overwritten with R and the tile reflectors, the
-    T factors, and the scratch buffer (which holds the device status word)."""
+    T factors, and the scratch buffer (which holds the device status word).
+    p is the number of panel domains (1 = flat tree)."""
 
-    def __init__(self, A, T, scratch, nb, ib):
-        self.A, self.T, self.scratch, self.nb, self.ib = A, T, scratch, nb, ib
+    def __init__(self, A, T, scratch, nb, ib, p=1):
+        self.A, self.T, self.scratch, self.nb, self.ib, self.p = A, T, scratch, nb, ib, p
         self.m, self.n = A.shape
 
     def R(self):
@@ -104,8 +106,18 @@ class Factorization:
         return qr_status(self.scratch, stream)
 
 
-def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None):
-    """Tile QR of A (in place). ``nb = 0`` uses the tuned table."""
+def qr_workspace_p(m, n, nb, ib, p, dtype=torch.float64):
+    """(t_elems, scratch_bytes) for qr_factor with p panel domains."""
+    t = ctypes.c_int64()
+    s = ctypes.c_int64()
+    _lib.check(lib().qr_workspace_p(m, n, nb, ib, p, _prec(dtype), ctypes.byref(t), ctypes.byref(s)),
+               "qr_workspace_p")
+    return t.value, s.value
+
+
+def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None, p=1):
+    """Tile QR of A (in place). ``nb = 0`` uses the tuned table; ``p > 1``
+    splits every panel into p domains merged by a binary tree."""
     m, n = A.shape
     if not A.is_cuda:
         raise ValueError("A must be a CUDA tensor")
@@ -114,6 +126,16 @@ def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None):
     lda = A.stride(1) if n > 1 else m
     if nb == 0:
         nb, ib = qr_lookup(m, n, A.dtype)
+    if p > 1:
+        t_elems, sbytes = qr_workspace_p(m, n, nb, ib, p, A.dtype)
+        if T is None or T.numel() < t_elems:
+            T = torch.empty(max(t_elems, 1), dtype=A.dtype, device=A.device)
+        if scratch is None or scratch.numel() < sbytes:
+            scratch = torch.empty(sbytes, dtype=torch.uint8, device=A.device)
+        f = lib().qr_factor_p_d if A.dtype == torch.float64 else lib().qr_factor_p_s
+        _lib.check(f(m, n, ctypes.c_void_p(A.data_ptr()), lda, nb, ib, p, ctypes.c_void_p(T.data_ptr()),
+                     ctypes.c_void_p(scratch.data_ptr()), sbytes, _stream_ptr(stream)), "qr_factor_p")
+        return Factorization(A, T, scratch, nb, ib, p)
     t_elems, sbytes = qr_workspace(m, n, nb, ib, A.dtype)
     if T is None or T.numel() < t_elems:
         T = torch.empty(max(t_elems, 1), dtype=A.dtype, device=A.device)
@@ -138,6 +160,15 @@ def qr_apply_qt(fact, C, trans=True, stream=None, parallel=True):
     ldc = C.stride(1) if nrhs > 1 else m
     f = lib().qr_apply_qt_d if C.dtype == torch.float64 else lib().qr_apply_qt_s
     lda = fact.A.stride(1) if n > 1 else m
+    if getattr(fact, "p", 1) > 1:
+        wb = ctypes.c_int64()
+        _lib.check(lib().qr_apply_workspace_p(m, n, nrhs, fact.nb, fact.p, ctypes.byref(wb)), "qr_apply_workspace_p")
+        ws = torch.empty(wb.value, dtype=torch.uint8, device=C.device)
+        f = lib().qr_apply_qt_p_d if C.dtype == torch.float64 else lib().qr_apply_qt_p_s
+        _lib.check(f(m, n, nrhs, ctypes.c_void_p(fact.A.data_ptr()), lda, fact.nb, fact.ib, fact.p,
+                     ctypes.c_void_p(fact.T.data_ptr()), ctypes.c_void_p(C.data_ptr()), ldc, 1 if trans else 0,
+                     ctypes.c_void_p(ws.data_ptr()), wb.value, _stream_ptr(stream)), "qr_apply_qt_p")
+        return C
     if parallel:
         wb = ctypes.c_int64()
         _lib.check(lib().qr_apply_workspace(m, n, nrhs, fact.nb, ctypes.byref(wb)), "qr_apply_workspace")
@@ -161,7 +192,7 @@ def form_q(fact, stream=None, parallel=True):
     return qr_apply_qt(fact, Q, trans=False, stream=stream, parallel=parallel)
 
 
-def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, work=None, stream=None):
+def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, work=None, stream=None, p=0):
     """min ||A X - B|| (A, B FP64, column-major CUDA tensors; unchanged).
     Returns (X, info) with info = (corrections, converged, device status)."""
     m, n = A.shape
@@ -173,7 +204,7 @@ def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, 
     if nb == 0:
         nb, ib = qr_lookup(m, n, torch.float32 if prec == QR_PREC_F32 else torch.float64)
     wb = ctypes.c_int64()
-    _lib.check(lib().qr_solve_ls_workspace(m, n, nrhs, prec, nb, ib, ctypes.byref(wb)), "qr_solve_ls_workspace")
+    _lib.check(lib().qr_solve_ls_workspace(m, n, nrhs, prec, nb, ib, p, ctypes.byref(wb)), "qr_solve_ls_workspace")
     if work is None or work.numel() < wb.value:
         work = torch.empty(wb.value, dtype=torch.uint8, device=A.device)
     X = colmajor_empty(n, nrhs, torch.float64, A.device)
@@ -182,7 +213,7 @@ def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, 
     ldb = B.stride(1) if nrhs > 1 else m
     ldx = X.stride(1) if nrhs > 1 else n
     _lib.check(lib().qr_solve_ls(m, n, nrhs, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(B.data_ptr()), ldb,
-                                 ctypes.c_void_p(X.data_ptr()), ldx, prec, nb, ib, max_iter, tol, info,
+                                 ctypes.c_void_p(X.data_ptr()), ldx, prec, nb, ib, p, max_iter, tol, info,
                                  ctypes.c_void_p(work.data_ptr()), wb.value, _stream_ptr(stream)), "qr_solve_ls")
     return X, tuple(info)
 

@@ -23,6 +23,14 @@ SIGNATURES = [
     ("qr_apply_qt_d", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp]),
     ("qr_apply_qt_s", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp]),
     ("qr_status", c_int, [c_vp, ctypes.POINTER(c_int), c_vp]),
+    ("qr_workspace_p", c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    ("qr_factor_p_d", c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_i64, c_vp]),
+    ("qr_factor_p_s", c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_i64, c_vp]),
+    ("qr_apply_workspace_p", c_int, [c_i64, c_i64, c_i64, c_int, c_int, ctypes.POINTER(c_i64)]),
+    ("qr_apply_qt_p_d", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp,
+                                c_i64, c_vp]),
+    ("qr_apply_qt_p_s", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp,
+                                c_i64, c_vp]),
     ("qr_apply_workspace", c_int, [c_i64, c_i64, c_i64, c_int, ctypes.POINTER(c_i64)]),
     ("qr_apply_qt_ws_d", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_vp, c_vp, c_i64, c_int, c_vp, c_i64,
                                  c_vp]),
@@ -36,9 +44,9 @@ SIGNATURES = [
     ("qr_batched_set_class", c_int, [c_int, c_int, c_int, c_int]),
     ("qr_batched_clear_classes", c_int, [c_int]),
     ("qr_batched_status", c_int, [c_vp, ctypes.POINTER(c_int), c_vp]),
-    ("qr_solve_ls_workspace", c_int, [c_i64, c_i64, c_i64, c_int, c_int, c_int, ctypes.POINTER(c_i64)]),
+    ("qr_solve_ls_workspace", c_int, [c_i64, c_i64, c_i64, c_int, c_int, c_int, c_int, ctypes.POINTER(c_i64)]),
     ("qr_solve_ls", c_int, [c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_int,
-                            c_dbl, ctypes.POINTER(c_int), c_vp, c_i64, c_vp]),
+                            c_int, c_dbl, ctypes.POINTER(c_int), c_vp, c_i64, c_vp]),
     ("qr_set_option", c_int, [c_int, c_i64]),
     ("qr_get_option", c_i64, [c_int]),
     ("qr_task_count", c_i64, [c_i64, c_i64, c_int, c_int]),

@@ -121,10 +121,14 @@ __device__ __forceinline__ S cta_sum(S v, S* red) {
 //
 // TR = true applies Q^T (blocks in ascending order, W <- T^T W); TR = false
 // applies Q (blocks in descending order, W <- T W).
+//
+// tri (TS mode only): the bottom reflectors are upper triangular -- the
+// triangle-on-triangle case of a tree reduction (TTQRT/TTMQR): V(r, c) is
+// taken as zero for r > c, whatever the tile holds there.
 template <typename S, bool TS, bool TR = true>
 __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, bool t_smem,
                          int lstart, int lend, int IB, S* Ctop, int ldct, S* C, int ldc, int rows,
-                         int c0, int c1, const Smem<S>& sm) {
+                         int c0, int c1, const Smem<S>& sm, bool tri = false) {
   if (c1 <= c0 || lend <= lstart || rows <= 0) return;
   const int tid = threadIdx.x;
   const int G = (rows + RPT - 1) / RPT;
@@ -140,7 +144,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
   // register. 16-byte copies need a leading dimension that is a multiple of
   // 16 bytes and a 16-byte aligned V.
   constexpr int EPC = 16 / sizeof(S);  // elements per 16-byte copy
-  const bool can_pipe = TS && (ldv % EPC == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0);
+  const bool can_pipe = TS && !tri && (ldv % EPC == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0);
   for (int cs = c0; cs < c1; cs += per) {
     const int cw = min(per, c1 - cs);
     const int g = tid / cw, c = tid - (tid / cw) * cw;
@@ -160,14 +164,17 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       const int rlo = TS ? 0 : l0;
       const int glo = rlo / RPT;
       const int rlo_al = glo * RPT;
-      const int nr = G * RPT - rlo_al;  // staged rows, zero-padded past `rows`
+      // triangle-on-triangle: this block's reflectors stop at row l0+ib-1, so
+      // the row groups below take no part in it
+      const int ghi = (TS && tri) ? min(G, (min(rows, l0 + ib) + RPT - 1) / RPT) : G;
+      const int nr = ghi * RPT - rlo_al;  // staged rows, zero-padded past `rows`
       S* vbuf = vcur ? sm.part : sm.vs;
       S* pbuf = vcur ? sm.vs : sm.part;
       const int vcap = vcur ? PART_CAP : VS_CAP;
       int PB = vcap / nr;
       if (PB > ib) PB = ib;
       if (PB < 1) PB = 1;
-      const bool myrows = act && g >= glo;
+      const bool myrows = act && g >= glo && g < ghi;
       // T_l in shared memory (ts) unless it is there already
       const bool t_in_ts = !t_smem && ib * ib <= TS_CAP;
       // --- phase A: W = Vfull^T Cstack, V staged PB reflectors at a time
@@ -181,7 +188,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
             S v = S(0);
             if (r < rows) {
               if (TS) {
-                v = ldg(V + r + (size_t)pc * ldv);
+                v = (tri && r > pc) ? S(0) : ldg(V + r + (size_t)pc * ldv);
               } else {
                 v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
               }
@@ -218,7 +225,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
             const int q = o / cw, cc = o - (o / cw) * cw;
             const int p = pp0 + pg0 + q;
             S s = TS ? ldg(Ctop + (l0 + p) + (size_t)(cs + cc) * ldct) : S(0);
-            for (int gg = glo; gg < G; ++gg) s += pbuf[(q * G + gg) * cw + cc];
+            for (int gg = glo; gg < ghi; ++gg) s += pbuf[(q * G + gg) * cw + cc];
             sm.w[p * cw + cc] = s;
           }
           __syncthreads();
@@ -301,7 +308,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
             S v = S(0);
             if (r < rows) {
               if (TS) {
-                v = ldg(V + r + (size_t)pc * ldv);
+                v = (tri && r > pc) ? S(0) : ldg(V + r + (size_t)pc * ldv);
               } else {
                 v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
               }
@@ -347,9 +354,11 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
 // V(r, q) for r in [0, nr): GE: unit at r = q, zero above (rows relative to
 // the block's first row); TS: full column (the stacked identity part is
 // orthogonal between reflectors and drops out of V^T V).
+// tri_off >= 0 (TS only): column q of V is zero below row tri_off + q
+// (triangle-on-triangle reflectors).
 template <typename S, bool TS>
 __device__ void build_t(const S* V, int ldv, bool v_smem, int nr, int ncol, const S* tau, S* Tout,
-                        int ldt, bool t_smem) {
+                        int ldt, bool t_smem, int tri_off = -1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // Gram entries z(q,p), q < p, into T's strict upper triangle
   const int npairs = ncol * (ncol - 1) / 2;
@@ -361,7 +370,8 @@ __device__ void build_t(const S* V, int ldv, bool v_smem, int nr, int ncol, cons
     const int q = pr - p * (p - 1) / 2;
     S s = S(0);
     const int r0 = TS ? 0 : p + 1;
-    for (int r = r0 + lane; r < nr; r += 32)
+    const int rend = (TS && tri_off >= 0) ? min(nr, tri_off + q + 1) : nr;
+    for (int r = r0 + lane; r < rend; r += 32)
       s = fma(ldx(V + r + (size_t)q * ldv, v_smem), ldx(V + r + (size_t)p * ldv, v_smem), s);
     s = warp_sum(s);
     if (lane == 0) {
@@ -414,10 +424,14 @@ __device__ void build_t(const S* V, int ldv, bool v_smem, int nr, int ncol, cons
 // FP32 working precision too: the Householder vector / tau generation is the
 // one place the mixed-precision path keeps FP64); the rank-1 updates run in S.
 template <typename S, bool TS>
-__device__ void panel_l2(S* P, int ldp, int nr, int w, S* Rs, int ldr, S* tau, S* red, int* bad) {
+__device__ void panel_l2(S* P, int ldp, int nr, int w, S* Rs, int ldr, S* tau, S* red, int* bad,
+                         int tri_off = -1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nr_all = nr;
   for (int jj = 0; jj < w; ++jj) {
     const int x0 = TS ? 0 : jj + 1;
+    // triangle-on-triangle: column jj of the bottom block has rows 0..tri_off+jj
+    nr = (TS && tri_off >= 0) ? min(nr_all, tri_off + jj + 1) : nr_all;
     S* col = P + (size_t)jj * ldp;
     // warp 0 forms the reflector: norm, beta, tau, scaling of x
     if (wid == 0) {
@@ -521,9 +535,14 @@ __device__ void geqrt(S* A, int lda, int rows, int cols, int IB, S* T, const Sme
 // TSQRT: QR of [R (upper triangle of the diagonal tile, ldr); B (rows x
 // cols, ldb)]. B receives the reflectors' lower parts, R the new triangle,
 // T (IB x cols) the block factors. Never touches R's strict lower part.
+//
+// tri = true is TTQRT, the triangle-on-triangle step of a reduction tree:
+// B's upper triangle is another R factor (its strict lower part belongs to
+// someone else and is neither read nor written); the reflectors then live in
+// B's upper triangle, column c having rows 0..c.
 template <typename S>
 __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, S* T, const Smem<S>& sm,
-                      int* bad) {
+                      int* bad, bool tri = false) {
   for (int l0 = 0; l0 < cols; l0 += IB) {
     const int ib = min(IB, cols - l0);
     int sb = PANEL_CAP / rows;
@@ -531,27 +550,28 @@ __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, 
     if (sb > 32) sb = 32;  // the R sub-block lives in rs (<= 32 x 32)
     for (int s0 = l0; s0 < l0 + ib; s0 += sb) {
       const int w = min(sb, l0 + ib - s0);
-      S* P = sm.part;  // rows x w
+      const int nr = tri ? min(rows, s0 + w) : rows;  // rows of B this sub-panel reaches
+      S* P = sm.part;  // nr x w
       __syncthreads();
-      for (int idx = threadIdx.x; idx < rows * w; idx += NTHREADS) {
-        const int cc = idx / rows, r = idx - cc * rows;
-        P[idx] = ldg(B + r + (size_t)(s0 + cc) * ldb);
+      for (int idx = threadIdx.x; idx < nr * w; idx += NTHREADS) {
+        const int cc = idx / nr, r = idx - cc * nr;
+        P[idx] = (tri && r > s0 + cc) ? S(0) : ldg(B + r + (size_t)(s0 + cc) * ldb);
       }
       for (int idx = threadIdx.x; idx < w * w; idx += NTHREADS) {
         const int cc = idx / w, r = idx - cc * w;
         sm.rs[idx] = (r <= cc) ? ldg(R + (s0 + r) + (size_t)(s0 + cc) * ldr) : S(0);
       }
       __syncthreads();
-      panel_l2<S, true>(P, rows, rows, w, sm.rs, w, sm.tau + (s0 - l0), sm.red, bad);
+      panel_l2<S, true>(P, nr, nr, w, sm.rs, w, sm.tau + (s0 - l0), sm.red, bad, tri ? s0 : -1);
       const bool whole = (w == ib);
       if (whole) {
-        build_t<S, true>(P, rows, true, rows, w, sm.tau, T + (size_t)l0 * IB, IB, false);
+        build_t<S, true>(P, nr, true, nr, w, sm.tau, T + (size_t)l0 * IB, IB, false, tri ? s0 : -1);
       } else if (s0 + w < l0 + ib) {
-        build_t<S, true>(P, rows, true, rows, w, sm.tau + (s0 - l0), sm.ts, w, true);
+        build_t<S, true>(P, nr, true, nr, w, sm.tau + (s0 - l0), sm.ts, w, true, tri ? s0 : -1);
       }
-      for (int idx = threadIdx.x; idx < rows * w; idx += NTHREADS) {
-        const int cc = idx / rows, r = idx - cc * rows;
-        stg(B + r + (size_t)(s0 + cc) * ldb, P[idx]);
+      for (int idx = threadIdx.x; idx < nr * w; idx += NTHREADS) {
+        const int cc = idx / nr, r = idx - cc * nr;
+        if (!tri || r <= s0 + cc) stg(B + r + (size_t)(s0 + cc) * ldb, P[idx]);
       }
       for (int idx = threadIdx.x; idx < w * w; idx += NTHREADS) {
         const int cc = idx / w, r = idx - cc * w;
@@ -559,17 +579,19 @@ __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, 
       }
       __syncthreads();
       if (!whole && s0 + w < l0 + ib) {
-        apply_qt<S, true>(B, ldb, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, R, ldr, B, ldb, rows,
-                          s0 + w, l0 + ib, sm);
+        apply_qt<S, true>(B, ldb, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, R, ldr, B, ldb, nr, s0 + w,
+                          l0 + ib, sm, tri);
       }
     }
+    const int nrb = tri ? min(rows, l0 + ib) : rows;  // rows the block's reflectors reach
     if (sb < ib) {
       __syncthreads();
-      build_t<S, true>(B + (size_t)l0 * ldb, ldb, false, rows, ib, sm.tau, T + (size_t)l0 * IB, IB, false);
+      build_t<S, true>(B + (size_t)l0 * ldb, ldb, false, nrb, ib, sm.tau, T + (size_t)l0 * IB, IB, false,
+                       tri ? l0 : -1);
     }
     __syncthreads();
     if (l0 + ib < cols)
-      apply_qt<S, true>(B, ldb, T, IB, false, l0, l0 + ib, IB, R, ldr, B, ldb, rows, l0 + ib, cols, sm);
+      apply_qt<S, true>(B, ldb, T, IB, false, l0, l0 + ib, IB, R, ldr, B, ldb, nrb, l0 + ib, cols, sm, tri);
     __syncthreads();
   }
 }
@@ -584,10 +606,13 @@ __device__ void unmqr(const S* V, int ldv, const S* T, int IB, int rows, int nre
 
 // TSMQR: [C1; C2] <- Q^T [C1; C2] for the TSQRT factors (V rows x nref in
 // the bottom tile, T IB x nref); C1 the top tile, C2 (rows) the bottom one.
+// tri = true is TTMQR: V holds triangle-on-triangle reflectors (upper
+// triangular), so only the first min(rows, nref) rows of C2 change.
 template <typename S>
 __device__ void tsmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C1, int ldc1, S* C2,
-                      int ldc2, int c0, int c1, const Smem<S>& sm) {
-  apply_qt<S, true>(V, ldv, T, IB, false, 0, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm);
+                      int ldc2, int c0, int c1, const Smem<S>& sm, bool tri = false) {
+  apply_qt<S, true>(V, ldv, T, IB, false, 0, nref, IB, C1, ldc1, C2, ldc2, tri ? min(rows, nref) : rows, c0, c1,
+                    sm, tri);
 }
 
 }  // namespace tqr

@@ -21,6 +21,8 @@
 #include <tuple>
 #include <vector>
 
+#include "layout.cuh"
+#include "listsched.h"
 #include "sched.cuh"
 #include "tile_kernels.cuh"
 #include "tileqr_internal.h"
@@ -33,6 +35,7 @@ std::mutex g_mu;
 int64_t g_wait_timeout_us = 20LL * 1000 * 1000;
 int g_ctas_per_sm = 0;
 int g_split = 0;
+int g_order = 1;  // ticket order of the flat tree: 0 earliest start time, 1 list schedule
 int g_grid_limit = 0;
 int64_t g_drop_task = -1;
 int g_record = 0;
@@ -91,8 +94,10 @@ Layout make_layout(int64_t m, int64_t n, int nb, int ib, size_t esz) {
 // flop weights, then a stable sort on it. Dependencies always start strictly
 // earlier, so the result is a topological order.
 struct SchedKey {
-  int MT, NT, S;
-  bool operator<(const SchedKey& o) const { return std::tie(MT, NT, S) < std::tie(o.MT, o.NT, o.S); }
+  int MT, NT, S, order;
+  bool operator<(const SchedKey& o) const {
+    return std::tie(MT, NT, S, order) < std::tie(o.MT, o.NT, o.S, o.order);
+  }
 };
 struct Sched {
   uint64_t* host = nullptr;  // pinned
@@ -101,7 +106,7 @@ struct Sched {
 std::map<SchedKey, Sched> g_sched;
 
 const Sched& get_schedule(int MT, int NT, int S) {
-  SchedKey key{MT, NT, S};
+  SchedKey key{MT, NT, S, g_order};
   auto it = g_sched.find(key);
   if (it != g_sched.end()) return it->second;
   const int K = std::min(MT, NT);
@@ -111,44 +116,98 @@ const Sched& get_schedule(int MT, int NT, int S) {
   est.reserve(code.capacity());
   std::vector<double> fin((size_t)MT * NT * S, 0.0);
   auto F = [&](int i, int j, int s) -> double& { return fin[((size_t)j * MT + i) * S + s]; };
+  // direct predecessors (last writers of the touched tile chunks) for the
+  // list-scheduled order
+  std::vector<int32_t> lastw((size_t)MT * NT * S, -1);
+  auto LW = [&](int i, int j, int s) -> int32_t& { return lastw[((size_t)j * MT + i) * S + s]; };
+  std::vector<int64_t> poff(1, 0);
+  std::vector<int32_t> pred;
+  std::vector<double> wt;
+  std::vector<int32_t> cur;
+  auto dep = [&](int i, int j, int s) {
+    const int32_t p = LW(i, j, s);
+    if (p >= 0 && std::find(cur.begin(), cur.end(), p) == cur.end()) cur.push_back(p);
+  };
+  auto close = [&](double w) {
+    for (int32_t p : cur) pred.push_back(p);
+    poff.push_back((int64_t)pred.size());
+    wt.push_back(w);
+    cur.clear();
+  };
   // relative costs (units of NB^3 flops); panel tasks run a latency-bound
   // level-2 part, so they are weighted up a little
   const double wG = 4.0 / 3.0 * 1.5, wT = 2.0 * 1.5, wU = 2.0 / S, wM = 4.0 / S;
   for (int k = 0; k < K; ++k) {
     {
       double st = 0;
-      for (int s = 0; s < S; ++s) st = std::max(st, F(k, k, s));
-      for (int s = 0; s < S; ++s) F(k, k, s) = st + wG;
+      for (int s = 0; s < S; ++s) {
+        st = std::max(st, F(k, k, s));
+        dep(k, k, s);
+      }
+      close(wG);
+      for (int s = 0; s < S; ++s) {
+        F(k, k, s) = st + wG;
+        LW(k, k, s) = (int32_t)code.size();
+      }
       code.push_back(encode_task(TASK_GEQRT, 0, k, k, k));
       est.push_back(st);
     }
     const double fin_geqrt = F(k, k, 0);
+    const int32_t geqrt_id = (int32_t)code.size() - 1;
     for (int j = k + 1; j < NT; ++j)
       for (int s = 0; s < S; ++s) {
         double st = std::max(fin_geqrt, F(k, j, s));
+        cur.push_back(geqrt_id);
+        dep(k, j, s);
+        close(wU);
         F(k, j, s) = st + wU;
+        LW(k, j, s) = (int32_t)code.size();
         code.push_back(encode_task(TASK_UNMQR, s, k, j, k));
         est.push_back(st);
       }
     for (int i = k + 1; i < MT; ++i) {
       double st = 0;
-      for (int s = 0; s < S; ++s) st = std::max(st, std::max(F(k, k, s), F(i, k, s)));
-      for (int s = 0; s < S; ++s) F(k, k, s) = F(i, k, s) = st + wT;
+      for (int s = 0; s < S; ++s) {
+        st = std::max(st, std::max(F(k, k, s), F(i, k, s)));
+        dep(k, k, s);
+        dep(i, k, s);
+      }
+      close(wT);
+      const int32_t ts_id = (int32_t)code.size();
+      for (int s = 0; s < S; ++s) {
+        F(k, k, s) = F(i, k, s) = st + wT;
+        LW(k, k, s) = LW(i, k, s) = ts_id;
+      }
       code.push_back(encode_task(TASK_TSQRT, 0, i, k, k));
       est.push_back(st);
       const double fin_v = st + wT;
       for (int j = k + 1; j < NT; ++j)
         for (int s = 0; s < S; ++s) {
           double st2 = std::max(fin_v, std::max(F(k, j, s), F(i, j, s)));
+          cur.push_back(ts_id);
+          dep(k, j, s);
+          dep(i, j, s);
+          close(wM);
           F(k, j, s) = F(i, j, s) = st2 + wM;
+          LW(k, j, s) = LW(i, j, s) = (int32_t)code.size();
           code.push_back(encode_task(TASK_TSMQR, s, i, j, k));
           est.push_back(st2);
         }
     }
   }
-  std::vector<int64_t> idx(code.size());
-  std::iota(idx.begin(), idx.end(), 0);
-  std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return est[a] < est[b]; });
+  std::vector<int64_t> idx;
+  if (g_order == 1) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    idx = list_schedule(wt, poff, pred, 2 * sms);
+  } else {
+    idx.resize(code.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return est[a] < est[b]; });
+  }
   Sched sc;
   sc.n = (int64_t)code.size();
   if (cudaHostAlloc((void**)&sc.host, sizeof(uint64_t) * std::max<int64_t>(sc.n, 1), cudaHostAllocDefault) !=
@@ -158,38 +217,6 @@ const Sched& get_schedule(int MT, int NT, int S) {
   }
   for (int64_t t = 0; t < sc.n; ++t) sc.host[t] = code[idx[t]];
   return g_sched.emplace(key, sc).first->second;
-}
-
-// ---------------------------------------------------------------------------
-// Device: layout conversion and status reset.
-template <typename S>
-__global__ void cm_to_tiles(const S* __restrict__ A, int64_t lda, int64_t m, int64_t n, S* __restrict__ W,
-                            int NB, int MT, int NT, unsigned* zero_words, int64_t nzero) {
-  const int64_t tile_elems = (int64_t)NB * NB;
-  const int64_t total = tile_elems * MT * NT;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int64_t t = e / tile_elems;
-    const int64_t w = e - t * tile_elems;
-    const int c = (int)(w / NB), r = (int)(w - (int64_t)c * NB);
-    const int j = (int)(t / MT), i = (int)(t - (int64_t)j * MT);
-    const int64_t row = (int64_t)i * NB + r, col = (int64_t)j * NB + c;
-    W[e] = (row < m && col < n) ? A[row + col * lda] : S(0);
-  }
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nzero; e += stride) zero_words[e] = 0u;
-}
-
-template <typename S>
-__global__ void tiles_to_cm(const S* __restrict__ W, S* __restrict__ A, int64_t lda, int64_t m, int64_t n,
-                            int NB, int MT) {
-  const int64_t total = m * n;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int64_t col = e / m, row = e - col * m;
-    const int i = (int)(row / NB), j = (int)(col / NB);
-    const int r = (int)(row - (int64_t)i * NB), c = (int)(col - (int64_t)j * NB);
-    A[row + col * lda] = W[((int64_t)j * MT + i) * NB * NB + r + (int64_t)c * NB];
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -578,6 +605,10 @@ int qr_set_option(int opt, int64_t value) {
     case QR_OPT_DROP_TASK:
       g_drop_task = value;
       return 0;
+    case QR_OPT_ORDER:
+      if (value != 0 && value != 1) return -2;
+      g_order = (int)value;
+      return 0;
   }
   return -1;
 }
@@ -591,6 +622,7 @@ int64_t qr_get_option(int opt) {
     case QR_OPT_GRID_LIMIT: return g_grid_limit;
     case QR_OPT_DROP_TASK: return g_drop_task;
     case QR_OPT_RECORD_EVENTS: return g_record;
+    case QR_OPT_ORDER: return g_order;
   }
   return INT64_MIN;
 }

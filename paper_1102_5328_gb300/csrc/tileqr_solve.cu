@@ -250,16 +250,24 @@ struct SolveLayout {
   int64_t cps;
 };
 
-SolveLayout solve_layout(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib) {
+// Panel domains for the solve's factorization when the caller passes p = 0:
+// about one domain per tile column's worth of tile rows (the flat-tree panel
+// chain of a tall matrix is MT tiles long), at most 32.
+int auto_domains(int64_t m, int64_t n, int nb) {
+  const int64_t MT = (m + nb - 1) / nb, NT = (n + nb - 1) / nb;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(32, (MT + NT - 1) / std::max<int64_t>(NT, 1)));
+}
+
+SolveLayout solve_layout(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib, int p) {
   SolveLayout L{};
   const size_t es = prec == QR_PREC_F32 ? 4 : 8;
-  qr_workspace(m, n, nb, ib, prec, &L.t_el, &L.sbytes);
+  qr_workspace_p(m, n, nb, ib, p, prec, &L.t_el, &L.sbytes);
   const int64_t k8 = std::min<int64_t>(nrhs, 8);
   size_t off = 0;
   L.a = off; off = al(off + (size_t)m * n * es);
   L.t = off; off = al(off + (size_t)L.t_el * es);
   L.scr = off; off = al(off + (size_t)L.sbytes);
-  qr_apply_workspace(m, n, std::min<int64_t>(nrhs, 8), nb, &L.apbytes);
+  qr_apply_workspace_p(m, n, std::min<int64_t>(nrhs, 8), nb, p, &L.apbytes);
   L.ap = off; off = al(off + (size_t)L.apbytes);
   L.bw = off; off = al(off + (size_t)m * k8 * es);
   L.hw = off; off = al(off + (size_t)n * k8 * es);
@@ -313,20 +321,20 @@ int trsm(int64_t n, const S* R, int64_t ldr, S* X, int64_t ldx, int nk, int tran
   return e == cudaSuccess ? 0 : (int)e;
 }
 
-// Q^T / Q through the dependency-ordered persistent application (few
-// right-hand sides still use many SMs).
+// Q^T / Q through the dependency-ordered persistent application over the
+// factorization's domain tree (few right-hand sides still use many SMs).
 template <typename S>
-int apply(int64_t m, int64_t n, int64_t nk, const S* A, int nb, int ib, const S* T, S* C, int trans, void* ws,
+int apply(int64_t m, int64_t n, int64_t nk, const S* A, int nb, int ib, int p, const S* T, S* C, int trans, void* ws,
           int64_t wsb, cudaStream_t st);
 template <>
-int apply<double>(int64_t m, int64_t n, int64_t nk, const double* A, int nb, int ib, const double* T, double* C,
+int apply<double>(int64_t m, int64_t n, int64_t nk, const double* A, int nb, int ib, int p, const double* T, double* C,
                   int trans, void* ws, int64_t wsb, cudaStream_t st) {
-  return qr_apply_qt_ws_d(m, n, nk, A, m, nb, ib, T, C, m, trans, ws, wsb, st);
+  return qr_apply_qt_p_d(m, n, nk, A, m, nb, ib, p, T, C, m, trans, ws, wsb, st);
 }
 template <>
-int apply<float>(int64_t m, int64_t n, int64_t nk, const float* A, int nb, int ib, const float* T, float* C, int trans,
-                 void* ws, int64_t wsb, cudaStream_t st) {
-  return qr_apply_qt_ws_s(m, n, nk, A, m, nb, ib, T, C, m, trans, ws, wsb, st);
+int apply<float>(int64_t m, int64_t n, int64_t nk, const float* A, int nb, int ib, int p, const float* T, float* C,
+                 int trans, void* ws, int64_t wsb, cudaStream_t st) {
+  return qr_apply_qt_p_s(m, n, nk, A, m, nb, ib, p, T, C, m, trans, ws, wsb, st);
 }
 
 // colmax wrote max|f| into scale[0..nk) and max|g| into scale[8..8+nk);
@@ -339,7 +347,7 @@ __global__ void merge_scale(int nk, double* scale) {
 // One group of <= 8 right-hand sides.
 template <typename S>
 int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, const double* B, int64_t ldb, double* X,
-                int64_t ldx, int prec, int nb, int ib, int max_iter, double tol, int* iters, int* converged,
+                int64_t ldx, int prec, int nb, int ib, int p, int max_iter, double tol, int* iters, int* converged,
                 const SolveLayout& L, char* w, cudaStream_t st) {
   S* Af = (S*)(w + L.a);
   S* T = (S*)(w + L.t);
@@ -371,13 +379,13 @@ int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, cons
     // R^T h = g/s
     if ((rc = trsm<S>(n, Af, m, Hw, n, nk, 1, st))) return rc;
     // d = Q^T f/s
-    if ((rc = apply<S>(m, n, nk, Af, nb, ib, T, Bw, 1, w + L.ap, L.apbytes, st))) return rc;
+    if ((rc = apply<S>(m, n, nk, Af, nb, ib, p, T, Bw, 1, w + L.ap, L.apbytes, st))) return rc;
     // Tw = d(0:n) - h ; Bw(0:n) = h
     split_correction<S><<<grid_for(n * nk), TB, 0, st>>>(m, n, nk, Bw, Hw, Tw);
     // R dx = Tw
     if ((rc = trsm<S>(n, Af, m, Tw, n, nk, 0, st))) return rc;
     // dr = Q [h; d(n:m)]
-    if ((rc = apply<S>(m, n, nk, Af, nb, ib, T, Bw, 0, w + L.ap, L.apbytes, st))) return rc;
+    if ((rc = apply<S>(m, n, nk, Af, nb, ib, p, T, Bw, 0, w + L.ap, L.apbytes, st))) return rc;
     if ((e = cudaMemsetAsync(sq, 0, 2 * 8 * 8, st)) != cudaSuccess) return (int)e;
     accumulate<S><<<dim3(64, nk), TB, 0, st>>>(n, nk, Tw, n, scale, x, n, sq);
     accumulate<S><<<dim3(256, nk), TB, 0, st>>>(m, nk, Bw, m, scale, r, m, nullptr);
@@ -414,19 +422,21 @@ int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, cons
 
 extern "C" {
 
-int qr_solve_ls_workspace(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib, int64_t* bytes) {
+int qr_solve_ls_workspace(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib, int p, int64_t* bytes) {
   if (m < 1) return -1;
   if (n < 1 || n > m) return -2;
   if (nrhs < 1) return -3;
   if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -4;
   if (nb == 0 && qr_lookup(m, n, prec, &nb, &ib) != 0) return -5;
-  if (!bytes) return -7;
-  *bytes = (int64_t)solve_layout(m, n, nrhs, prec, nb, ib).total;
+  if (!bytes) return -8;
+  if (p < 0 || p > 4096) return -6;
+  if (p == 0) p = auto_domains(m, n, nb);
+  *bytes = (int64_t)solve_layout(m, n, nrhs, prec, nb, ib, p).total;
   return 0;
 }
 
 int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* B, int64_t ldb,
-                double* X, int64_t ldx, int prec, int nb, int ib, int max_iter, double tol, int* info,
+                double* X, int64_t ldx, int prec, int nb, int ib, int p, int max_iter, double tol, int* info,
                 void* d_work, int64_t work_bytes, void* stream) {
   if (m < 1) return -1;
   if (n < 1 || n > m) return -2;
@@ -441,20 +451,22 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda
   if (nb == 0 && qr_lookup(m, n, prec, &nb, &ib) != 0) return -11;
   if (nb < 8 || nb > 512) return -11;
   if (ib < 1 || ib > nb || ib > 256) return -12;
-  if (!d_work) return -16;
+  if (p < 0 || p > 4096) return -13;
+  if (p == 0) p = auto_domains(m, n, nb);
+  if (!d_work) return -17;
   cudaStream_t st = (cudaStream_t)stream;
-  const SolveLayout L = solve_layout(m, n, nrhs, prec, nb, ib);
-  if (work_bytes < (int64_t)L.total) return -17;
+  const SolveLayout L = solve_layout(m, n, nrhs, prec, nb, ib, p);
+  if (work_bytes < (int64_t)L.total) return -18;
   char* w = (char*)d_work;
   cudaError_t e;
   int rc;
   // factor the working-precision copy
   if (prec == QR_PREC_F64) {
     cvt<double, double><<<grid_for(m * n), TB, 0, st>>>(m, n, A, lda, (double*)(w + L.a), m);
-    rc = qr_factor_d(m, n, (double*)(w + L.a), m, nb, ib, (double*)(w + L.t), w + L.scr, L.sbytes, st);
+    rc = qr_factor_p_d(m, n, (double*)(w + L.a), m, nb, ib, p, (double*)(w + L.t), w + L.scr, L.sbytes, st);
   } else {
     cvt<double, float><<<grid_for(m * n), TB, 0, st>>>(m, n, A, lda, (float*)(w + L.a), m);
-    rc = qr_factor_s(m, n, (float*)(w + L.a), m, nb, ib, (float*)(w + L.t), w + L.scr, L.sbytes, st);
+    rc = qr_factor_p_s(m, n, (float*)(w + L.a), m, nb, ib, p, (float*)(w + L.t), w + L.scr, L.sbytes, st);
   }
   if (rc) return rc;
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
@@ -462,9 +474,9 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda
   for (int64_t k0 = 0; k0 < nrhs; k0 += 8) {
     const int nk = (int)std::min<int64_t>(8, nrhs - k0);
     rc = prec == QR_PREC_F64
-             ? solve_group<double>(m, n, nk, A, lda, B + (size_t)k0 * ldb, ldb, X + (size_t)k0 * ldx, ldx, prec, nb, ib,
+             ? solve_group<double>(m, n, nk, A, lda, B + (size_t)k0 * ldb, ldb, X + (size_t)k0 * ldx, ldx, prec, nb, ib, p,
                                    max_iter, tol, &iters, &conv, L, w, st)
-             : solve_group<float>(m, n, nk, A, lda, B + (size_t)k0 * ldb, ldb, X + (size_t)k0 * ldx, ldx, prec, nb, ib,
+             : solve_group<float>(m, n, nk, A, lda, B + (size_t)k0 * ldb, ldb, X + (size_t)k0 * ldx, ldx, prec, nb, ib, p,
                                   max_iter, tol, &iters, &conv, L, w, st);
     if (rc) return rc;
   }
