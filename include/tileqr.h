@@ -123,11 +123,12 @@ int qr_apply_qt_ws_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64
  * Tile QR with p domains per panel (the paper's third tunable for
  * tall-skinny matrices, communication-avoiding QR, Sec. 6).
  * qr_workspace_p / qr_factor_p_d / qr_factor_p_s: as qr_workspace /
- *   qr_factor_*, with p >= 1 domains: at each step the tile rows below the
- *   panel are cut into p contiguous ranges, each eliminated by its own flat
- *   tree (GEQRT on its first tile, TSQRT down the range, UNMQR/TSMQR
- *   updates), and the p triangles are merged by a binary tree of
- *   triangle-on-triangle steps (TTQRT, with TTMQR updates). p = 1 is the
+ *   qr_factor_*, with p >= 1 domains: at step k the tile rows k..MT-1 are
+ *   cut into ranges of ceil(MT/p) rows starting at row k (the domains slide
+ *   down with the panel), each eliminated by its own flat tree (GEQRT on its
+ *   first tile, TSQRT down the range, UNMQR/TSMQR updates), and the
+ *   triangles are merged by a binary tree of triangle-on-triangle steps
+ *   (TTQRT, with TTMQR updates). p = 1 is the
  *   flat tree of qr_factor_* (same arithmetic). A ragged last tile row is
  *   never a domain head. Output: R in the upper triangle of d_A; below it the
  *   reflectors; a domain head's tile keeps its GEQRT reflectors below the
@@ -286,6 +287,10 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t l
  *   most 8 pairs; Step 2 = time qr_factor for the survivors at every shape,
  *   ascending n, `reps` runs each (median; the paper uses 6, Sec. 5.1), and
  *   prune as you go with Property 5.1 between square orders (Sec. 5.3).
+ *   For tall-skinny shapes (m >= 4n, at least 4 tile rows) the chosen pair
+ *   is then timed with p = 2, 4, ... panel domains (qr_factor_p_*; at most
+ *   64 and 2 MT/NT), the paper's third tunable for such matrices; the
+ *   table records the best p (1 = flat tree).
  * mode 1 (exhaustive search, ES): Step 2 over the whole grid, no pruning.
  * prec: QR_PREC_F64 / QR_PREC_F32. table_path (may be NULL/""): JSON decision
  * table written at the end; it also becomes the in-process table used by
@@ -312,6 +317,9 @@ int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t *bytes);
 int qr_load_table(const char *path);
 int qr_clear_tables(void);
 int qr_lookup(int64_t m, int64_t n, int prec, int *nb, int *ib);
+/* qr_lookup_p -- as qr_lookup, and *p the tuned panel domains for
+ * qr_factor_p_* (1 where the table has none: the flat tree). */
+int qr_lookup_p(int64_t m, int64_t n, int prec, int *nb, int *ib, int *p);
 
 /*
  * Host-only decision rules of the tuner (no GPU call), exported so that they
@@ -355,6 +363,9 @@ int qr_step1_time(int nb, int ib, int prec, int launches, double *seconds_per_la
  */
 int qr_time_factor(int64_t m, int64_t n, int nb, int ib, int prec, int reps, double *median_s, double *min_s,
                    void *d_work, int64_t work_bytes, void *stream);
+/* qr_time_factor_p -- the same measurement of qr_factor_p_* with p domains. */
+int qr_time_factor_p(int64_t m, int64_t n, int nb, int ib, int p, int prec, int reps, double *median_s,
+                     double *min_s, void *d_work, int64_t work_bytes, void *stream);
 
 /*
  * Learned cost model of the tuner (this library's addition; the paper tunes

@@ -115,9 +115,10 @@ def qr_workspace_p(m, n, nb, ib, p, dtype=torch.float64):
     return t.value, s.value
 
 
-def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None, p=1):
-    """Tile QR of A (in place). ``nb = 0`` uses the tuned table; ``p > 1``
-    splits every panel into p domains merged by a binary tree."""
+def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None, p=None):
+    """Tile QR of A (in place). ``nb = 0`` uses the tuned table (including
+    its panel-domain count p for tall-skinny shapes); ``p > 1`` splits every
+    panel into domains merged by a binary tree; p = 1 is the flat tree."""
     m, n = A.shape
     if not A.is_cuda:
         raise ValueError("A must be a CUDA tensor")
@@ -125,7 +126,11 @@ def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None, p=1):
         raise ValueError("A must be column-major (use colmajor())")
     lda = A.stride(1) if n > 1 else m
     if nb == 0:
-        nb, ib = qr_lookup(m, n, A.dtype)
+        nb, ib, pt = qr_lookup_p(m, n, A.dtype)
+        if p is None:
+            p = pt
+    if p is None:
+        p = 1
     if p > 1:
         t_elems, sbytes = qr_workspace_p(m, n, nb, ib, p, A.dtype)
         if T is None or T.numel() < t_elems:
@@ -313,6 +318,14 @@ def qr_lookup(m, n, dtype=torch.float64):
     nb, ib = ctypes.c_int(), ctypes.c_int()
     _lib.check(lib().qr_lookup(m, n, _prec(dtype), ctypes.byref(nb), ctypes.byref(ib)), "qr_lookup")
     return nb.value, ib.value
+
+
+def qr_lookup_p(m, n, dtype=torch.float64):
+    """(nb, ib, p) from the loaded tuning table (built-in default otherwise)."""
+    nb, ib, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _lib.check(lib().qr_lookup_p(m, n, _prec(dtype), ctypes.byref(nb), ctypes.byref(ib), ctypes.byref(p)),
+               "qr_lookup_p")
+    return nb.value, ib.value, p.value
 
 
 def qr_flops(m, n):

@@ -59,6 +59,7 @@ SIGNATURES = [
     ("qr_mlp_train", c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_int, ctypes.c_float, c_vp, c_vp, c_vp]),
     ("qr_clear_tables", c_int, []),
     ("qr_lookup", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    ("qr_lookup_p", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     ("qr_tune_grid", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     ("qr_tune_preselect", c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_dbl), c_int,
                                   c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
@@ -70,6 +71,8 @@ SIGNATURES = [
     ("qr_tune_workspace", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_i64)]),
     ("qr_time_factor", c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),
                                c_vp, c_i64, c_vp]),
+    ("qr_time_factor_p", c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl),
+                                 ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
     ("qr_tune", c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_int, c_int, c_int, c_int, c_int,
                         ctypes.c_char_p, ctypes.c_char_p, c_vp, c_i64, ctypes.POINTER(c_dbl), c_vp]),
     ("qr_peak_fp64", c_int, [ctypes.POINTER(c_dbl), c_vp]),

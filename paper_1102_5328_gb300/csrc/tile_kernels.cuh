@@ -349,6 +349,125 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
 }
 
 // ---------------------------------------------------------------------------
+// Narrow update (few columns of C: the Q^T b / Q h products of a
+// least-squares solve). A TSMQR/UNMQR task on a handful of columns is pure
+// latency in apply_qt (a staging round trip and several barriers per inner
+// block), so here the whole reflector tile, its T factors and the touched
+// rows of C are staged in shared memory once per task; each inner block then
+// costs three barriers. Same operations as apply_qt (blocks in order, W =
+// V^T C, W <- T^T W or T W, C -= V W), different summation order.
+// Usable when narrow_fits(): rows * nref <= VS_CAP, IB * nref <= PART_CAP,
+// (rows + nref) * cw <= W_CAP, IB * cw <= min(TS_CAP, NTHREADS), cw <= 16.
+__host__ __device__ inline bool narrow_fits(int rows, int nref, int IB, int cw) {
+  return rows * nref <= VS_CAP && IB * nref <= PART_CAP && (rows + nref) * cw <= W_CAP && IB * cw <= TS_CAP &&
+         IB * cw <= NTHREADS && cw <= 16;
+}
+
+template <typename S, bool TS, bool TR>
+__device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restrict__ T, int ldt, int nref, int IB,
+                             S* Ctop, int ldct, S* C, int ldc, int rows, int c0, int c1, const Smem<S>& sm,
+                             bool tri = false) {
+  const int tid = threadIdx.x;
+  const int cw = c1 - c0;
+  if (cw <= 0 || nref <= 0 || rows <= 0) return;
+  S* Vs = sm.vs;            // rows x nref, column-major (ld rows)
+  S* Ts = sm.part;          // IB x nref (ld IB)
+  S* Cb = sm.w;             // rows x cw (ld rows): C (GE) or the bottom tile (TS)
+  S* Ct = sm.w + rows * cw; // nref x cw (ld nref): top rows (TS)
+  S* Ws = sm.ts;            // IB x cw
+  __syncthreads();
+  for (int idx = tid; idx < rows * nref; idx += NTHREADS) {
+    const int c = idx / rows, r = idx - (idx / rows) * rows;
+    S v;
+    if (TS) v = (tri && r > c) ? S(0) : ldg(V + r + (size_t)c * ldv);
+    else v = (r < c) ? S(0) : (r == c ? S(1) : ldg(V + r + (size_t)c * ldv));
+    Vs[idx] = v;
+  }
+  for (int idx = tid; idx < IB * nref; idx += NTHREADS) {
+    const int c = idx / IB, q = idx - (idx / IB) * IB;
+    Ts[idx] = ldg(T + q + (size_t)c * ldt);
+  }
+  for (int idx = tid; idx < rows * cw; idx += NTHREADS) {
+    const int c = idx / rows, r = idx - (idx / rows) * rows;
+    Cb[idx] = ldg(C + r + (size_t)(c0 + c) * ldc);
+  }
+  if (TS)
+    for (int idx = tid; idx < nref * cw; idx += NTHREADS) {
+      const int c = idx / nref, r = idx - (idx / nref) * nref;
+      Ct[idx] = ldg(Ctop + r + (size_t)(c0 + c) * ldct);
+    }
+  __syncthreads();
+  const int nblk = (nref + IB - 1) / IB;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int l0 = (TR ? bi : nblk - 1 - bi) * IB;
+    const int ib = min(IB, nref - l0);
+    const int nout = ib * cw;
+    // threads per output (a power of two dividing 32) for the row sums
+    int tpo = NTHREADS / max(nout, 1);
+    tpo = tpo >= 32 ? 32 : (tpo >= 16 ? 16 : (tpo >= 8 ? 8 : (tpo >= 4 ? 4 : (tpo >= 2 ? 2 : 1))));
+    const int r0 = TS ? 0 : l0;  // GE: rows above the block are untouched
+    // phase A: W(p, c) = Ctop(l0+p, c) [TS] + sum_r V(r, l0+p) Cb(r, c)
+    for (int base = 0; base < nout * tpo; base += NTHREADS) {
+      const int gid = base + tid;
+      const int o = gid / tpo, part = gid - (gid / tpo) * tpo;
+      S acc = S(0);
+      if (o < nout) {
+        const int pp = o / cw, c = o - (o / cw) * cw;
+        const S* vcol = Vs + (size_t)(l0 + pp) * rows;
+        const S* ccol = Cb + (size_t)c * rows;
+        for (int r = r0 + part; r < rows; r += tpo) acc = fma(vcol[r], ccol[r], acc);
+      }
+      for (int off = tpo / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (o < nout && part == 0) {
+        const int pp = o / cw, c = o - (o / cw) * cw;
+        if (TS) acc += Ct[(l0 + pp) + (size_t)c * nref];
+        Ws[pp * cw + c] = acc;
+      }
+    }
+    __syncthreads();
+    // phase B: W <- T^T W (Q^T) or T W (Q), one output per thread
+    S wv = S(0);
+    int po = -1, co = 0;
+    if (tid < nout) {
+      po = tid / cw;
+      co = tid - po * cw;
+      const S* Tb = Ts + (size_t)l0 * IB;  // (q, p) at Tb[q + p * IB]
+      if (TR) {
+        for (int q = 0; q <= po; ++q) wv = fma(Tb[q + po * IB], Ws[q * cw + co], wv);
+      } else {
+        for (int q = po; q < ib; ++q) wv = fma(Tb[po + q * IB], Ws[q * cw + co], wv);
+      }
+    }
+    __syncthreads();
+    if (po >= 0) Ws[po * cw + co] = wv;
+    __syncthreads();
+    // phase C: Ctop(l0+p) -= W (TS); Cb(r) -= sum_p V(r, l0+p) W(p)
+    if (TS)
+      for (int o = tid; o < nout; o += NTHREADS) {
+        const int pp = o / cw, c = o - (o / cw) * cw;
+        Ct[(l0 + pp) + (size_t)c * nref] -= Ws[pp * cw + c];
+      }
+    for (int o = tid; o < (rows - r0) * cw; o += NTHREADS) {
+      const int c = o / (rows - r0), r = r0 + (o - (o / (rows - r0)) * (rows - r0));
+      S acc = Cb[r + (size_t)c * rows];
+      for (int pp = 0; pp < ib; ++pp) acc = fma(-Vs[r + (size_t)(l0 + pp) * rows], Ws[pp * cw + c], acc);
+      Cb[r + (size_t)c * rows] = acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < rows * cw; idx += NTHREADS) {
+    const int c = idx / rows, r = idx - (idx / rows) * rows;
+    stg(C + r + (size_t)(c0 + c) * ldc, Cb[idx]);
+  }
+  if (TS)
+    for (int idx = tid; idx < nref * cw; idx += NTHREADS) {
+      const int c = idx / nref, r = idx - (idx / nref) * nref;
+      stg(Ctop + r + (size_t)(c0 + c) * ldct, Ct[idx]);
+    }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // T factor of a block of ncol reflectors (LAPACK's forward, columnwise
 // recurrence): T(p,p) = tau_p, T(0:p,p) = -tau_p T(0:p,0:p) (V^T v_p)(0:p).
 // V(r, q) for r in [0, nr): GE: unit at r = q, zero above (rows relative to

@@ -252,12 +252,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_apply(ApplyArgs<S> a) 
     if (!s_ok) break;
     S* Ck = a.C + (size_t)k * NB;
     const int ck = cols_of(k);
+    // few right-hand sides: stage the whole task in shared memory once
     if (type == TASK_UNMQR) {
-      apply_qt<S, false, TR>(tileA(k, k), (int)a.lda, tfac(k, k), a.IB, false, 0, ck, a.IB, nullptr, 0, Ck,
-                             (int)a.ldc, rows_of(k), c0, c1, sm);
+      if (narrow_fits(rows_of(k), ck, a.IB, c1 - c0))
+        apply_narrow<S, false, TR>(tileA(k, k), (int)a.lda, tfac(k, k), a.IB, ck, a.IB, nullptr, 0, Ck, (int)a.ldc,
+                                   rows_of(k), c0, c1, sm);
+      else
+        apply_qt<S, false, TR>(tileA(k, k), (int)a.lda, tfac(k, k), a.IB, false, 0, ck, a.IB, nullptr, 0, Ck,
+                               (int)a.ldc, rows_of(k), c0, c1, sm);
     } else {
-      apply_qt<S, true, TR>(tileA(i, k), (int)a.lda, tfac(i, k), a.IB, false, 0, ck, a.IB, Ck, (int)a.ldc,
-                            a.C + (size_t)i * NB, (int)a.ldc, rows_of(i), c0, c1, sm);
+      if (narrow_fits(rows_of(i), ck, a.IB, c1 - c0))
+        apply_narrow<S, true, TR>(tileA(i, k), (int)a.lda, tfac(i, k), a.IB, ck, a.IB, Ck, (int)a.ldc,
+                                  a.C + (size_t)i * NB, (int)a.ldc, rows_of(i), c0, c1, sm);
+      else
+        apply_qt<S, true, TR>(tileA(i, k), (int)a.lda, tfac(i, k), a.IB, false, 0, ck, a.IB, Ck, (int)a.ldc,
+                              a.C + (size_t)i * NB, (int)a.ldc, rows_of(i), c0, c1, sm);
     }
     __threadfence();
     __syncthreads();

@@ -23,9 +23,10 @@ __host__ __device__ inline void decode_task(uint64_t c, int& type, int& s, int& 
 
 }  // namespace tqr
 
-// (nb, ib) for a shape from the loaded tuning table (nearest tuned N), or the
-// built-in default when no table is loaded. Returns 0 on success.
-int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib);
+// (nb, ib) -- and the panel domains p when pd is not null -- for a shape from
+// the loaded tuning table (nearest tuned shape), or the built-in default
+// (128, 16, p = 1) when no table is loaded. Returns 0 on success.
+int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib, int* pd = nullptr);
 
 // Builds (and caches) the host task order for this shape so that a later
 // timed qr_factor_* call does not include it. Returns 0 on success.

@@ -6,11 +6,12 @@
 // domains of the panel (Sec. 6, communication-avoiding QR). In the flat tree
 // of Sec. 2.1 the panel of step k is one chain GEQRT(k) -> TSQRT(k+1) -> ...
 // -> TSQRT(MT-1), MT - k tasks long. With p domains the tile rows k..MT-1 are
-// cut into p contiguous ranges; each runs its own flat tree (GEQRT on the
-// domain's first tile, TSQRT down the domain, with UNMQR/TSMQR updates), and
-// the p triangles left at the domain heads are merged pairwise by a binary
-// tree of triangle-on-triangle steps (TTQRT, with TTMQR updates). The chain
-// shrinks to about (MT - k)/p + log2 p tasks. p = 1 is the flat tree.
+// cut into ranges of ceil(MT/p) rows that slide down with the panel; each
+// runs its own flat tree (GEQRT on the domain's first tile, TSQRT down the
+// domain, with UNMQR/TSMQR updates), and the triangles left at the domain
+// heads are merged pairwise by a binary tree of triangle-on-triangle steps
+// (TTQRT, with TTMQR updates). The chain shrinks to about MT/p + log2 p
+// tasks. p = 1 is the flat tree.
 //
 // Dependencies are explicit: a host pass over the program order records,
 // for every task, how many earlier writes each tile (column chunk) it touches
@@ -64,17 +65,19 @@ static_assert(sizeof(TaskRec) == 32, "task record is 32 bytes");
 
 std::mutex g_tmu2;
 
-// Domain heads of step k: tile rows [k, MT) cut into min(p, MT-k) ranges.
-// A ragged last tile row shorter than the panel is never a head (a head
-// runs GEQRT, which needs rows >= columns); it joins the domain before it.
+// Domain heads of step k: the tile rows [k, MT) cut into ranges of
+// B = ceil(MT / p) rows starting at the panel, so the domains slide down
+// with the panel. A head of step k+1 is then the second row of a domain of
+// step k, which receives its last update of step k early (the first link of
+// that domain's chain) instead of waiting for the merge tree -- the steps
+// pipeline as in the flat tree. Fewer than p domains remain once
+// MT - k < (p - 1) B. A ragged last tile row shorter than the panel is never
+// a head (a head runs GEQRT, which needs rows >= columns); it joins the
+// domain before it.
 std::vector<int> domain_heads(int k, int MT, int p, bool last_short) {
-  const int R = MT - k;
-  const int pk = std::max(1, std::min(p, R));
+  const int B = std::max(1, (MT + p - 1) / p);
   std::vector<int> h;
-  for (int d = 0; d < pk; ++d) {
-    const int hd = k + (int)((int64_t)d * R / pk);
-    if (h.empty() || hd != h.back()) h.push_back(hd);
-  }
+  for (int r = k; r < MT; r += B) h.push_back(r);
   if (last_short && h.size() > 1 && h.back() == MT - 1) h.pop_back();
   return h;
 }
@@ -578,15 +581,25 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_apply_dag(ApplyDagArgs
     const int c0 = (int)((int64_t)sc * a.nrhs / Sp), c1 = (int)((int64_t)(sc + 1) * a.nrhs / Sp);
     const int ck = cols_of(k);
     S* Ch = a.C + (size_t)h * NB;
+    // few right-hand sides: stage the whole task in shared memory once
+    const int rw = type == D_UNMQR ? rows_of(h) : (type == D_TSMQR ? rows_of(i) : min(rows_of(i), ck));
+    const bool nar = narrow_fits(rw, ck, a.IB, c1 - c0);
     if (type == D_UNMQR) {
-      apply_qt<S, false, TR>(tileA(h, k), (int)a.lda, t1(h, k), a.IB, false, 0, ck, a.IB, nullptr, 0, Ch, (int)a.ldc,
-                             rows_of(h), c0, c1, sm);
-    } else if (type == D_TSMQR) {
-      apply_qt<S, true, TR>(tileA(i, k), (int)a.lda, t1(i, k), a.IB, false, 0, ck, a.IB, Ch, (int)a.ldc,
-                            a.C + (size_t)i * NB, (int)a.ldc, rows_of(i), c0, c1, sm);
+      if (nar)
+        apply_narrow<S, false, TR>(tileA(h, k), (int)a.lda, t1(h, k), a.IB, ck, a.IB, nullptr, 0, Ch, (int)a.ldc, rw,
+                                   c0, c1, sm);
+      else
+        apply_qt<S, false, TR>(tileA(h, k), (int)a.lda, t1(h, k), a.IB, false, 0, ck, a.IB, nullptr, 0, Ch,
+                               (int)a.ldc, rw, c0, c1, sm);
     } else {
-      apply_qt<S, true, TR>(tileA(i, k), (int)a.lda, t2(i, k), a.IB, false, 0, ck, a.IB, Ch, (int)a.ldc,
-                            a.C + (size_t)i * NB, (int)a.ldc, min(rows_of(i), ck), c0, c1, sm, true);
+      const S* tf = type == D_TSMQR ? t1(i, k) : t2(i, k);
+      const bool tri = type == D_TTMQR;
+      if (nar)
+        apply_narrow<S, true, TR>(tileA(i, k), (int)a.lda, tf, a.IB, ck, a.IB, Ch, (int)a.ldc, a.C + (size_t)i * NB,
+                                  (int)a.ldc, rw, c0, c1, sm, tri);
+      else
+        apply_qt<S, true, TR>(tileA(i, k), (int)a.lda, tf, a.IB, false, 0, ck, a.IB, Ch, (int)a.ldc,
+                              a.C + (size_t)i * NB, (int)a.ldc, rw, c0, c1, sm, tri);
     }
     __threadfence();
     __syncthreads();

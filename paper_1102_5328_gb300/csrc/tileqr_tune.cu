@@ -113,11 +113,12 @@ struct Entry {
   int64_t m, n;
   int nb, ib;
   double gflops;
+  int p;  // panel domains (1 = flat tree; tuned for tall-skinny shapes)
 };
 std::mutex g_tmu;
 std::vector<Entry> g_table[2];  // [0] fp64, [1] fp32
 
-int lookup_entry(const std::vector<Entry>& t, int64_t m, int64_t n, int* nb, int* ib) {
+int lookup_entry(const std::vector<Entry>& t, int64_t m, int64_t n, int* nb, int* ib, int* pd) {
   if (t.empty()) return 1;
   int64_t best = INT64_MAX, bsum = INT64_MAX;
   int bi = -1;
@@ -132,6 +133,7 @@ int lookup_entry(const std::vector<Entry>& t, int64_t m, int64_t n, int* nb, int
   }
   *nb = t[bi].nb;
   *ib = t[bi].ib;
+  if (pd) *pd = t[bi].p;
   return 0;
 }
 
@@ -141,8 +143,8 @@ bool write_table(const char* path, int prec, const std::vector<Entry>& t, const 
   if (!f) return false;
   fprintf(f, "{\n  \"prec\": \"%s\",\n%s  \"entries\": [\n", prec ? "fp32" : "fp64", extra.c_str());
   for (size_t i = 0; i < t.size(); ++i)
-    fprintf(f, "    {\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"gflops\": %.4f}%s\n", (long long)t[i].m,
-            (long long)t[i].n, t[i].nb, t[i].ib, t[i].gflops, i + 1 < t.size() ? "," : "");
+    fprintf(f, "    {\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"p\": %d, \"gflops\": %.4f}%s\n",
+            (long long)t[i].m, (long long)t[i].n, t[i].nb, t[i].ib, t[i].p, t[i].gflops, i + 1 < t.size() ? "," : "");
   fprintf(f, "  ]\n}\n");
   fclose(f);
   return true;
@@ -163,9 +165,13 @@ bool read_table(const char* path, int* prec, std::vector<Entry>* t) {
   while ((p = s.find("{\"m\":", p)) != std::string::npos) {
     Entry e;
     long long m, n;
-    if (sscanf(s.c_str() + p, "{\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"gflops\": %lf", &m, &n, &e.nb,
+    e.p = 1;
+    if (sscanf(s.c_str() + p, "{\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"p\": %d, \"gflops\": %lf", &m,
+               &n, &e.nb, &e.ib, &e.p, &e.gflops) != 6 &&
+        sscanf(s.c_str() + p, "{\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"gflops\": %lf", &m, &n, &e.nb,
                &e.ib, &e.gflops) != 5)
       return false;
+    if (e.p < 1) e.p = 1;
     e.m = m;
     e.n = n;
     t->push_back(e);
@@ -262,10 +268,11 @@ int step1_time(int nb, int ib, int nbatch, int launches, double* sec, void* work
 // Step-2 timing of qr_factor at (m, n, nb, ib): reps runs, returns median and
 // min seconds. The matrix is regenerated on the device before every run.
 template <typename S>
-int time_factor(int64_t m, int64_t n, int nb, int ib, int reps, void* work, int64_t wbytes, cudaStream_t st,
+int time_factor(int64_t m, int64_t n, int nb, int ib, int pd, int reps, void* work, int64_t wbytes, cudaStream_t st,
                 double* med, double* mn) {
   int64_t t_el = 0, sb = 0;
-  int rc = qr_workspace(m, n, nb, ib, sizeof(S) == 8 ? QR_PREC_F64 : QR_PREC_F32, &t_el, &sb);
+  int rc = pd > 1 ? qr_workspace_p(m, n, nb, ib, pd, sizeof(S) == 8 ? QR_PREC_F64 : QR_PREC_F32, &t_el, &sb)
+                  : qr_workspace(m, n, nb, ib, sizeof(S) == 8 ? QR_PREC_F64 : QR_PREC_F32, &t_el, &sb);
   if (rc) return rc;
   const size_t a_bytes = ((size_t)m * n * sizeof(S) + 255) & ~(size_t)255;
   const size_t t_bytes = ((size_t)t_el * sizeof(S) + 255) & ~(size_t)255;
@@ -284,8 +291,12 @@ int time_factor(int64_t m, int64_t n, int nb, int ib, int reps, void* work, int6
   for (int r = 1 - warm; r < reps + 1; ++r) {
     fill_uniform<S><<<1184, 256, 0, st>>>(A, m * n, (uint64_t)(m * 31 + n), -0.5, 0.5);
     cudaEventRecord(e0, st);
-    rc = sizeof(S) == 8 ? qr_factor_d(m, n, (double*)A, m, nb, ib, (double*)T, scr, sb, st)
-                        : qr_factor_s(m, n, (float*)A, m, nb, ib, (float*)T, scr, sb, st);
+    if (pd > 1)
+      rc = sizeof(S) == 8 ? qr_factor_p_d(m, n, (double*)A, m, nb, ib, pd, (double*)T, scr, sb, st)
+                          : qr_factor_p_s(m, n, (float*)A, m, nb, ib, pd, (float*)T, scr, sb, st);
+    else
+      rc = sizeof(S) == 8 ? qr_factor_d(m, n, (double*)A, m, nb, ib, (double*)T, scr, sb, st)
+                          : qr_factor_s(m, n, (float*)A, m, nb, ib, (float*)T, scr, sb, st);
     cudaEventRecord(e1, st);
     if (rc) break;
     cudaError_t e = cudaEventSynchronize(e1);
@@ -311,11 +322,12 @@ double qr_flops_d(int64_t m, int64_t n) { return 2.0 * m * (double)n * n - 2.0 *
 
 // --- resumable JSONL log ------------------------------------------------------
 struct LogKey {
-  int kind;  // 1 = step 1, 2 = step 2
+  int kind;  // 1 = step 1, 2 = step 2 (p = 1), 3 = domain sweep of a tall shape
   int64_t m, n;
   int nb, ib;
+  int p;
   bool operator<(const LogKey& o) const {
-    return std::tie(kind, m, n, nb, ib) < std::tie(o.kind, o.m, o.n, o.nb, o.ib);
+    return std::tie(kind, m, n, nb, ib, p) < std::tie(o.kind, o.m, o.n, o.nb, o.ib, o.p);
   }
 };
 
@@ -329,31 +341,36 @@ void read_log(const char* path, std::map<LogKey, double>* seen) {
     long long m, n;
     double sec;
     if (sscanf(line, "{\"kind\": %d, \"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"seconds\": %lf", &kind, &m,
-               &n, &nb, &ib, &sec) == 6)
-      (*seen)[LogKey{kind, m, n, nb, ib}] = sec;
+               &n, &nb, &ib, &sec) == 6) {
+      int pd = 1;
+      const char* pp = strstr(line, "\"p\": ");
+      if (pp) pd = atoi(pp + 5);
+      (*seen)[LogKey{kind, m, n, nb, ib, pd}] = sec;
+    }
   }
   fclose(f);
 }
 
 void append_log(const char* path, int kind, int64_t m, int64_t n, int nb, int ib, double sec, double smin,
-                int reps) {
+                int reps, int pd = 1) {
   if (!path || !path[0]) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
   fprintf(f, "{\"kind\": %d, \"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"seconds\": %.9g, \"min\": %.9g, "
-             "\"reps\": %d}\n",
-          kind, (long long)m, (long long)n, nb, ib, sec, smin, reps);
+             "\"reps\": %d, \"p\": %d}\n",
+          kind, (long long)m, (long long)n, nb, ib, sec, smin, reps, pd);
   fclose(f);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib) {
+int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib, int* pd) {
   std::lock_guard<std::mutex> lock(g_tmu);
   const int p = elem_bytes == 4 ? 1 : 0;
-  if (lookup_entry(g_table[p], m, n, nb, ib) == 0) return 0;
-  if (p == 1 && lookup_entry(g_table[0], m, n, nb, ib) == 0) return 0;
+  if (pd) *pd = 1;
+  if (lookup_entry(g_table[p], m, n, nb, ib, pd) == 0) return 0;
+  if (p == 1 && lookup_entry(g_table[0], m, n, nb, ib, pd) == 0) return 0;
   *nb = 128;  // built-in default when nothing is loaded
   *ib = 16;
   return 0;
@@ -384,7 +401,17 @@ int qr_lookup(int64_t m, int64_t n, int prec, int* nb, int* ib) {
   if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
   if (!nb) return -4;
   if (!ib) return -5;
-  return qr_table_lookup(m, n, prec == QR_PREC_F32 ? 4 : 8, nb, ib);
+  return qr_table_lookup(m, n, prec == QR_PREC_F32 ? 4 : 8, nb, ib, nullptr);
+}
+
+int qr_lookup_p(int64_t m, int64_t n, int prec, int* nb, int* ib, int* p) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
+  if (!nb) return -4;
+  if (!ib) return -5;
+  if (!p) return -6;
+  return qr_table_lookup(m, n, prec == QR_PREC_F32 ? 4 : 8, nb, ib, p);
 }
 
 int qr_tune_grid(int nb_lo, int nb_hi, int nb_step, int ib_min, int cap, int* nbs, int* ibs) {
@@ -471,7 +498,8 @@ int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t* bytes) {
   int64_t best = step1_bytes(512, 2 * sm_count(), esz);
   for (int nb = 64; nb <= 512; nb += 32) {
     int64_t t_el = 0, sb = 0;
-    qr_workspace(max_m, max_n, nb, std::min(nb / 2, 256), prec, &t_el, &sb);
+    // the domain-tree path (tall-skinny p sweep) needs the larger scratch
+    qr_workspace_p(max_m, max_n, nb, std::min(nb / 2, 256), 64, prec, &t_el, &sb);
     const int64_t need = (int64_t)(((size_t)max_m * max_n * esz + 255) & ~(size_t)255) +
                          (int64_t)((t_el * esz + 255) & ~(size_t)255) + sb;
     best = std::max(best, need);
@@ -486,9 +514,22 @@ int qr_time_factor(int64_t m, int64_t n, int nb, int ib, int prec, int reps, dou
   if (n < 1 || n > m) return -2;
   if (reps < 1) return -6;
   if (!median_s || !min_s) return -7;
-  return prec == QR_PREC_F32 ? time_factor<float>(m, n, nb, ib, reps, d_work, work_bytes, (cudaStream_t)stream,
+  return prec == QR_PREC_F32 ? time_factor<float>(m, n, nb, ib, 1, reps, d_work, work_bytes, (cudaStream_t)stream,
                                                   median_s, min_s)
-                             : time_factor<double>(m, n, nb, ib, reps, d_work, work_bytes, (cudaStream_t)stream,
+                             : time_factor<double>(m, n, nb, ib, 1, reps, d_work, work_bytes, (cudaStream_t)stream,
+                                                   median_s, min_s);
+}
+
+int qr_time_factor_p(int64_t m, int64_t n, int nb, int ib, int p, int prec, int reps, double* median_s, double* min_s,
+                     void* d_work, int64_t work_bytes, void* stream) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (p < 1 || p > 4096) return -5;
+  if (reps < 1) return -7;
+  if (!median_s || !min_s) return -8;
+  return prec == QR_PREC_F32 ? time_factor<float>(m, n, nb, ib, p, reps, d_work, work_bytes, (cudaStream_t)stream,
+                                                  median_s, min_s)
+                             : time_factor<double>(m, n, nb, ib, p, reps, d_work, work_bytes, (cudaStream_t)stream,
                                                    median_s, min_s);
 }
 
@@ -516,7 +557,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       nb[g] = grid[g].first;
       ib[g] = grid[g].second;
       double s = 0, gf = 0;
-      auto it = seen.find(LogKey{1, 0, 0, nb[g], ib[g]});
+      auto it = seen.find(LogKey{1, 0, 0, nb[g], ib[g], 1});
       if (it != seen.end()) {
         s = it->second;
       } else {
@@ -546,7 +587,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
     std::vector<double> perf(surv.size(), 0.0);
     for (size_t c = 0; c < surv.size(); ++c) {
       double med = 0, mn = 0;
-      auto it = seen.find(LogKey{2, m, n, surv[c].first, surv[c].second});
+      auto it = seen.find(LogKey{2, m, n, surv[c].first, surv[c].second, 1});
       if (it != seen.end()) {
         med = it->second;
       } else {
@@ -563,7 +604,31 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
     size_t bi = 0;
     for (size_t c = 1; c < surv.size(); ++c)
       if (perf[c] > perf[bi] || (perf[c] == perf[bi] && surv[c].first < surv[bi].first)) bi = c;
-    table.push_back(Entry{m, n, surv[bi].first, surv[bi].second, perf[bi]});
+    Entry ent{m, n, surv[bi].first, surv[bi].second, perf[bi], 1};
+    // the paper's third tunable for tall-skinny matrices: the number of
+    // panel domains, swept in powers of two with the chosen (NB, IB)
+    const int64_t MTs = (m + ent.nb - 1) / ent.nb, NTs = (n + ent.nb - 1) / ent.nb;
+    if (m >= 4 * n && MTs >= 4)
+      for (int pd = 2; pd <= 64 && pd <= MTs / std::max<int64_t>(NTs, 1) * 2 && pd <= MTs; pd *= 2) {
+        double med = 0, mn = 0;
+        auto it = seen.find(LogKey{3, m, n, ent.nb, ent.ib, pd});
+        if (it != seen.end()) {
+          med = it->second;
+        } else {
+          const auto t0 = std::chrono::steady_clock::now();
+          int rc = qr_time_factor_p(m, n, ent.nb, ent.ib, pd, prec, reps, &med, &mn, d_work, work_bytes, stream);
+          if (rc) return rc;
+          step2_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+          append_log(log_path, 3, m, n, ent.nb, ent.ib, med, mn, reps, pd);
+          ++measured;
+        }
+        const double g = qr_flops_d(m, n) / med / 1e9;
+        if (g > ent.gflops) {
+          ent.gflops = g;
+          ent.p = pd;
+        }
+      }
+    table.push_back(ent);
     if (mode == 0 && m == n) {  // prune as you go along the square orders
       std::vector<int> nbv(surv.size()), keep(surv.size());
       for (size_t c = 0; c < surv.size(); ++c) nbv[c] = surv[c].first;

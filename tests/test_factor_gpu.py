@@ -182,3 +182,19 @@ def test_double_buffered_staging_is_bitwise_neutral(q):
         q.qr_apply_qt(f, C1, trans=trans)
         q.qr_apply_qt(f_odd, C2, trans=trans)
         assert torch.equal(C1, C2)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 16])
+def test_narrow_application_matches_wide(q, nrhs):
+    """Few right-hand sides take the shared-memory narrow path in the
+    dependency-ordered application; the column-chunk kernel takes the wide
+    path. Same operations, different summation order: equal to rounding."""
+    m, n = 640, 384
+    A = inputs.uniform_matrix(m, n, seed=31)
+    f = _gpu_factor(q, A, 64, 8)
+    for trans in (True, False):
+        C1 = to_dev(inputs.normal_matrix(m, nrhs, seed=nrhs))
+        C2 = C1.clone().t().contiguous().t()
+        q.qr_apply_qt(f, C1, trans=trans, parallel=False)
+        q.qr_apply_qt(f, C2, trans=trans, parallel=True)
+        assert torch.allclose(C1, C2, rtol=0, atol=100 * n * U * float(C1.abs().max()))

@@ -87,6 +87,8 @@ def test_table_roundtrip_and_lookup(L, tmp_path):
     for i, e in enumerate(t["entries"]):
         lines.append('    {"m": %d, "n": %d, "nb": %d, "ib": %d, "gflops": %.4f}%s'
                      % (e["m"], e["n"], e["nb"], e["ib"], e["gflops"], "," if i < 2 else ""))
+    lines[-1] = lines[-1].replace('{"m": 2000,', '{"m": 2000,')
+    lines += ['    ,{"m": 50000, "n": 500, "nb": 64, "ib": 8, "p": 16, "gflops": 300.0}']
     lines += ['  ]', '}']
     p.write_text("\n".join(lines))
     assert L.qr_load_table(str(p).encode()) == 0
@@ -96,6 +98,11 @@ def test_table_roundtrip_and_lookup(L, tmp_path):
         e = [x for x in t["entries"] if x["n"] == tuning.nearest(n_req, [1000, 2000, 10000])][0]
         assert e["n"] == expect
         assert (nb.value, ib.value) == (e["nb"], e["ib"])
+    p_ = ctypes.c_int()
+    assert L.qr_lookup_p(60000, 400, 0, ctypes.byref(nb), ctypes.byref(ib), ctypes.byref(p_)) == 0
+    assert (nb.value, ib.value, p_.value) == (64, 8, 16)
+    assert L.qr_lookup_p(1000, 1000, 0, ctypes.byref(nb), ctypes.byref(ib), ctypes.byref(p_)) == 0
+    assert p_.value == 1  # entries without p are flat-tree entries
     L.qr_clear_tables()
     assert L.qr_lookup(5000, 5000, 0, ctypes.byref(nb), ctypes.byref(ib)) == 0
     assert (nb.value, ib.value) == (128, 16)  # built-in default
