@@ -252,17 +252,21 @@ def run_ls(args):
     B = torch.from_numpy(np.ascontiguousarray(B_np.T)).cuda().t()
     res = {}
     for name, prec, it in (("fp64", q.QR_PREC_F64, 0), ("mixed_fp32_ir", q.QR_PREC_F32, 50)):
-        nb, ib = (args.nb, args.ib) if args.nb else q.qr_lookup(m, n, torch.float64)
+        dt = torch.float32 if prec == q.QR_PREC_F32 else torch.float64
+        nb, ib, pd = q.qr_lookup_p(m, n, dt)
+        if args.nb:
+            nb, ib = args.nb, args.ib
+        pd = args.ls_p if args.ls_p else pd
         tol = args.ls_tol if prec == q.QR_PREC_F32 else 2.0 ** -52
-        X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it, tol=tol, p=args.ls_p)  # warm-up
+        X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it, tol=tol, p=pd)  # warm-up
         torch.cuda.synchronize()
         ts = []
         for _ in range(max(args.steps, 3)):
             t0 = time.perf_counter()
-            X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it, tol=tol, p=args.ls_p)
+            X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it, tol=tol, p=pd)
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
-        res[name] = {"median_s": statistics.median(ts), "info": list(info), "nb": nb, "ib": ib, "tol": tol,
+        res[name] = {"median_s": statistics.median(ts), "info": list(info), "nb": nb, "ib": ib, "p": pd, "tol": tol,
                      "X": X.cpu().numpy()}
     line = {"workload": "least squares %dx%d, kappa 1e6, %d RHS N(0,1)" % (m, n, k), "metric": "seconds per solve"}
     if not args.no_cpu:
@@ -334,7 +338,7 @@ def main():
     ap.add_argument("--ls-n", type=int, default=4096)
     ap.add_argument("--ls-tol", type=float, default=1e-11,
                     help="mixed solve: stop once ||dx|| <= tol ||x|| (FP64-level accuracy for kappa 1e6)")
-    ap.add_argument("--ls-p", type=int, default=0, help="panel domains of the solve's factorization (0 = auto)")
+    ap.add_argument("--ls-p", type=int, default=0, help="panel domains of the solve's factorization (0 = the tuned table's p)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -199,7 +199,10 @@ def form_q(fact, stream=None, parallel=True):
 
 def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, work=None, stream=None, p=0):
     """min ||A X - B|| (A, B FP64, column-major CUDA tensors; unchanged).
-    Returns (X, info) with info = (corrections, converged, device status)."""
+    ``nb = 0`` takes (nb, ib) from the tuned table of the factorization's
+    precision, and p too when ``p = 0`` (the C library's p = 0 picks
+    ceil(MT/NT) domains). Returns (X, info) with info = (corrections,
+    converged, device status)."""
     m, n = A.shape
     nrhs = B.shape[1]
     if A.dtype != torch.float64 or B.dtype != torch.float64:
@@ -207,7 +210,8 @@ def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, 
     if A.stride(0) != 1 or B.stride(0) != 1:
         raise ValueError("A and B must be column-major")
     if nb == 0:
-        nb, ib = qr_lookup(m, n, torch.float32 if prec == QR_PREC_F32 else torch.float64)
+        nb, ib, tp = qr_lookup_p(m, n, torch.float32 if prec == QR_PREC_F32 else torch.float64)
+        p = p if p else tp
     wb = ctypes.c_int64()
     _lib.check(lib().qr_solve_ls_workspace(m, n, nrhs, prec, nb, ib, p, ctypes.byref(wb)), "qr_solve_ls_workspace")
     if work is None or work.numel() < wb.value:
