@@ -33,6 +33,11 @@ import numpy as np  # noqa: E402
 N_DEFAULT = 10000
 SEED = 10000
 
+# DRAM bytes (read + write) of one persistent_qr<double> launch, from one
+# ncu capture of the same configuration and kernel sources
+# (profiles/persistent_qr_fp64_n10000.md); None for any other configuration.
+TRAFFIC_BYTES = {(10000, 10000, 128, 8): 68.35e9 + 41.85e9}
+
 
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -427,7 +432,7 @@ def main():
         "achieved": achieved, "peak": nominal_peak, "unit": "TFLOP/s", "frac": achieved / nominal_peak,
         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
         "peak_measured_live": peak_live / 1e3, "frac_of_measured": achieved / (peak_live / 1e3),
-        "traffic": None, "kernel_ms_avg": kavg,
+        "traffic": TRAFFIC_BYTES.get((m, n, nb, ib)), "kernel_ms_avg": kavg,
     }
 
     e2e = None
