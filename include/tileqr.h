@@ -186,6 +186,22 @@ int qr_factor_d_noalloc(int64_t m, int64_t n, double *d_A, int64_t lda, int nb, 
  */
 int qr_status(const void *d_scratch, int *status, void *stream);
 
+/*
+ * qr_set_trace -- per-task trace of the persistent factorization and Q
+ * application kernels (diagnostics; the paper's runs are timed as a whole).
+ * d_buf: device array (32-byte aligned) of `capacity` records of four
+ * uint64: task index in the launch's ticket order (bits 0..39), task type
+ * (bits 40..47: 0 GEQRT, 1 UNMQR, 2 TSQRT, 3 TSMQR, 4 TTQRT, 5 TTMQR) and SM
+ * id (bits 48..63); %globaltimer (ns) when the ticket was taken, when the
+ * task's dependencies were met, and when its completion was published. Every later
+ * launch of persistent_qr, persistent_qr_dag or persistent_apply_dag writes
+ * record t for its task t < capacity (overwriting the previous launch's);
+ * the caller owns the buffer and reads it after synchronising. NULL (or
+ * capacity 0) turns tracing off. Returns -1 for a misaligned buffer, -2 for
+ * a negative capacity.
+ */
+int qr_set_trace(void *d_buf, int64_t capacity);
+
 /* qr_set_option / qr_get_option -- process-wide settings (QR_OPT_*). */
 int qr_set_option(int opt, int64_t value);
 int64_t qr_get_option(int opt);
@@ -263,7 +279,9 @@ int qr_batched_status(const void *d_scratch, int *status, void *stream);
  *   the corrections stopped shrinking (no column's correction fell below
  *   half the previous one, from the third correction on: the limiting
  *   accuracy of FP64 residuals is reached), 0 if max_iter ran out first;
- *   device status bits.
+ *   device status bits (QR_DEV_*: of the factorization, and QR_DEV_TIMEOUT
+ *   from the triangular solves, whose row blocks wait on each other with
+ *   the same bounded waits as the scheduler).
  * d_work (>= qr_solve_ls_workspace bytes) is caller-owned. Synchronises
  * `stream` once per correction (stopping test) and at the end.
  */

@@ -297,6 +297,29 @@ def qr_set_option(opt, value):
     _lib.check(lib().qr_set_option(opt, int(value)), "qr_set_option")
 
 
+def qr_set_trace(buf=None):
+    """Per-task trace of the persistent kernels into ``buf`` (a CUDA int64
+    tensor of shape (capacity, 4), see read_trace); None turns it off."""
+    if buf is None:
+        _lib.check(lib().qr_set_trace(None, 0), "qr_set_trace")
+    else:
+        if buf.dtype != torch.int64 or buf.dim() != 2 or buf.shape[1] != 4 or not buf.is_contiguous():
+            raise ValueError("trace buffer must be a contiguous int64 tensor of shape (capacity, 4)")
+        _lib.check(lib().qr_set_trace(ctypes.c_void_p(buf.data_ptr()), buf.shape[0]), "qr_set_trace")
+
+
+def read_trace(buf, ntasks):
+    """Records 0..ntasks-1 of a trace buffer as NumPy arrays: task, type,
+    sm, t_take, t_ready, t_done (ns, relative to the earliest t_take)."""
+    r = buf[:ntasks].cpu().numpy().view("uint64")
+    task = (r[:, 0] & ((1 << 40) - 1)).astype("int64")
+    typ = ((r[:, 0] >> 40) & 0xFF).astype("int64")
+    sm = (r[:, 0] >> 48).astype("int64")
+    t0 = r[:, 1].min()
+    return (task, typ, sm, (r[:, 1] - t0).astype("int64"), (r[:, 2] - t0).astype("int64"),
+            (r[:, 3] - t0).astype("int64"))
+
+
 def qr_get_option(opt):
     return lib().qr_get_option(opt)
 

@@ -77,6 +77,45 @@ __device__ __forceinline__ void stx(S* p, S v, bool sm) {
   if (sm) *p = v; else __stcg(p, v);
 }
 
+// Copy of a rows x cols column-major block from global memory (ld lds,
+// L2-coherent loads) into shared memory (ld ldd). Each thread issues U loads
+// before its first store, so a thread has U global loads in flight instead
+// of one load-store round trip per element. Element (r, c) is read only if
+// rd(r, c) (else taken as 0); f(r, c, v) gives the value stored (masks such
+// as the unit diagonal).
+template <int U, typename S, typename R, typename F>
+__device__ __forceinline__ void stage_block(S* dst, int ldd, const S* src, int64_t lds, int rows, int cols, R rd,
+                                            F f) {
+  const int total = rows * cols;
+  for (int base = threadIdx.x; base < total; base += U * NTHREADS) {
+    S v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NTHREADS;
+      v[u] = S(0);
+      if (idx < total) {
+        const int c = idx / rows, r = idx - c * rows;
+        if (rd(r, c)) v[u] = __ldcg(src + r + (size_t)c * lds);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * NTHREADS;
+      if (idx < total) {
+        const int c = idx / rows, r = idx - c * rows;
+        dst[r + (size_t)c * ldd] = f(r, c, v[u]);
+      }
+    }
+  }
+}
+struct AllRd {
+  __device__ bool operator()(int, int) const { return true; }
+};
+struct Ident {
+  template <typename S>
+  __device__ S operator()(int, int, S v) const { return v; }
+};
+
 template <typename S>
 __device__ __forceinline__ S warp_sum(S v) {
 #pragma unroll
@@ -99,6 +138,29 @@ __device__ __forceinline__ S cta_sum(S v, S* red) {
   }
   __syncthreads();
   return red[NTHREADS / 32];
+}
+
+// Reflectors pc0 .. pc0+pb-1 of a tile V (ld ldv), rows r0 .. r0+nr-1, into
+// buf (ld nr) with their masks (GE: zero above the diagonal, unit diagonal;
+// TS tri: zero below it); zero past `rows`. GE: four loads in flight per
+// thread. TS: one (its later blocks come through the cp.async prefetch of
+// apply_qt, and the TS update keeps more registers live).
+template <typename S, bool TS>
+__device__ __forceinline__ void stage_refl(S* buf, const S* V, int ldv, int nr, int r0, int rows, int pc0, int pb,
+                                           bool tri) {
+  if constexpr (TS) {
+    for (int idx = threadIdx.x; idx < pb * nr; idx += NTHREADS) {
+      const int p = idx / nr, rl = idx - (idx / nr) * nr;
+      const int r = rl + r0, pc = pc0 + p;
+      S v = S(0);
+      if (r < rows) v = (tri && r > pc) ? S(0) : ldg(V + r + (size_t)pc * ldv);
+      buf[p * nr + rl] = v;
+    }
+  } else {
+    stage_block<4>(buf, nr, V + r0 + (size_t)pc0 * ldv, ldv, nr, pb,
+                   [=](int rl, int p) { return rl + r0 < rows && rl + r0 > pc0 + p; },
+                   [=](int rl, int p, S v) { return rl + r0 == pc0 + p ? S(1) : v; });
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -182,19 +244,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         const int pb = min(PB, ib - pp0);
         if (!staged) {
           __syncthreads();
-          for (int idx = tid; idx < pb * nr; idx += NTHREADS) {
-            const int p = idx / nr, rl = idx - (idx / nr) * nr;
-            const int r = rl + rlo_al, pc = l0 + pp0 + p;
-            S v = S(0);
-            if (r < rows) {
-              if (TS) {
-                v = (tri && r > pc) ? S(0) : ldg(V + r + (size_t)pc * ldv);
-              } else {
-                v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
-              }
-            }
-            vbuf[p * nr + rl] = v;
-          }
+          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri);
           if (pp0 == 0 && t_in_ts)
             for (int idx = tid; idx < ib * ib; idx += NTHREADS) {
               const int p = idx / ib, q = idx - (idx / ib) * ib;
@@ -209,12 +259,30 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
 #pragma unroll
             for (int q = 0; q < PG; ++q) acc[q] = S(0);
             const S* vrow = vbuf + (size_t)pg0 * nr + (g * RPT - rlo_al);
+            if constexpr (sizeof(S) == 4) {
+              // FP32: 16-byte shared loads (4 rows of a reflector) feed 4
+              // FMAs each; vbuf, nr and the row offset are multiples of 4
+              // elements, and the summation order per reflector is unchanged
 #pragma unroll
-            for (int rr = 0; rr < RPT; ++rr) {
-              const S cv = creg[rr];
+              for (int r4 = 0; r4 < RPT; r4 += 4) {
 #pragma unroll
-              for (int q = 0; q < PG; ++q)
-                if (q < pgc) acc[q] = fma(vrow[q * nr + rr], cv, acc[q]);
+                for (int q = 0; q < PG; ++q)
+                  if (q < pgc) {
+                    const float4 v = *reinterpret_cast<const float4*>(vrow + q * nr + r4);
+                    acc[q] = fma(v.x, creg[r4], acc[q]);
+                    acc[q] = fma(v.y, creg[r4 + 1], acc[q]);
+                    acc[q] = fma(v.z, creg[r4 + 2], acc[q]);
+                    acc[q] = fma(v.w, creg[r4 + 3], acc[q]);
+                  }
+              }
+            } else {
+#pragma unroll
+              for (int rr = 0; rr < RPT; ++rr) {
+                const S cv = creg[rr];
+#pragma unroll
+                for (int q = 0; q < PG; ++q)
+                  if (q < pgc) acc[q] = fma(vrow[q * nr + rr], cv, acc[q]);
+              }
             }
 #pragma unroll
             for (int q = 0; q < PG; ++q)
@@ -302,19 +370,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         const int pb = min(PB, ib - pp0);
         if (PB < ib) {
           __syncthreads();
-          for (int idx = tid; idx < pb * nr; idx += NTHREADS) {
-            const int p = idx / nr, rl = idx - (idx / nr) * nr;
-            const int r = rl + rlo_al, pc = l0 + pp0 + p;
-            S v = S(0);
-            if (r < rows) {
-              if (TS) {
-                v = (tri && r > pc) ? S(0) : ldg(V + r + (size_t)pc * ldv);
-              } else {
-                v = (r < pc) ? S(0) : (r == pc ? S(1) : ldg(V + r + (size_t)pc * ldv));
-              }
-            }
-            vbuf[p * nr + rl] = v;
-          }
+          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri);
           __syncthreads();
         }
         if (myrows) {
@@ -322,8 +378,19 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
           for (int p = 0; p < pb; ++p) {
             const S wv = sm.w[(pp0 + p) * cw + c];
             const S* vp = vrow + (size_t)p * nr;
+            if constexpr (sizeof(S) == 4) {
 #pragma unroll
-            for (int rr = 0; rr < RPT; ++rr) creg[rr] = fma(-vp[rr], wv, creg[rr]);
+              for (int r4 = 0; r4 < RPT; r4 += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(vp + r4);
+                creg[r4] = fma(-v.x, wv, creg[r4]);
+                creg[r4 + 1] = fma(-v.y, wv, creg[r4 + 1]);
+                creg[r4 + 2] = fma(-v.z, wv, creg[r4 + 2]);
+                creg[r4 + 3] = fma(-v.w, wv, creg[r4 + 3]);
+              }
+            } else {
+#pragma unroll
+              for (int rr = 0; rr < RPT; ++rr) creg[rr] = fma(-vp[rr], wv, creg[rr]);
+            }
           }
         }
       }
@@ -363,10 +430,28 @@ __host__ __device__ inline bool narrow_fits(int rows, int nref, int IB, int cw) 
          IB * cw <= NTHREADS && cw <= 16;
 }
 
+// The reflector tile and its T factors of an apply_narrow task into shared
+// memory (sm.vs, sm.part). A caller whose V and T are final before the
+// task's C rows are (the Q application after the factorization) issues this
+// before waiting for C and passes vt_staged = true to apply_narrow. Ends
+// without a barrier; the caller's barrier (or apply_narrow's) follows.
+template <typename S, bool TS>
+__device__ void narrow_stage_vt(const S* __restrict__ V, int ldv, const S* __restrict__ T, int ldt, int nref, int IB,
+                                int rows, const Smem<S>& sm, bool tri = false) {
+  // reflectors with their masks (TS tri: zero below the diagonal; GE: zero
+  // above it, unit diagonal); every element read lies inside the tile
+  if (TS)
+    stage_block<16>(sm.vs, rows, V, ldv, rows, nref, [tri](int r, int c) { return !(tri && r > c); }, Ident());
+  else
+    stage_block<16>(sm.vs, rows, V, ldv, rows, nref, [](int r, int c) { return r > c; },
+                    [](int r, int c, S v) { return r == c ? S(1) : v; });
+  stage_block<8>(sm.part, IB, T, ldt, IB, nref, AllRd(), Ident());
+}
+
 template <typename S, bool TS, bool TR>
 __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restrict__ T, int ldt, int nref, int IB,
                              S* Ctop, int ldct, S* C, int ldc, int rows, int c0, int c1, const Smem<S>& sm,
-                             bool tri = false) {
+                             bool tri = false, bool vt_staged = false) {
   const int tid = threadIdx.x;
   const int cw = c1 - c0;
   if (cw <= 0 || nref <= 0 || rows <= 0) return;
@@ -375,27 +460,35 @@ __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restri
   S* Cb = sm.w;             // rows x cw (ld rows): C (GE) or the bottom tile (TS)
   S* Ct = sm.w + rows * cw; // nref x cw (ld nref): top rows (TS)
   S* Ws = sm.ts;            // IB x cw
+  S* W2 = sm.ts + NTHREADS; // IB x cw (IB * cw <= NTHREADS), T applied
   __syncthreads();
-  for (int idx = tid; idx < rows * nref; idx += NTHREADS) {
-    const int c = idx / rows, r = idx - (idx / rows) * rows;
-    S v;
-    if (TS) v = (tri && r > c) ? S(0) : ldg(V + r + (size_t)c * ldv);
-    else v = (r < c) ? S(0) : (r == c ? S(1) : ldg(V + r + (size_t)c * ldv));
-    Vs[idx] = v;
-  }
-  for (int idx = tid; idx < IB * nref; idx += NTHREADS) {
-    const int c = idx / IB, q = idx - (idx / IB) * IB;
-    Ts[idx] = ldg(T + q + (size_t)c * ldt);
-  }
-  for (int idx = tid; idx < rows * cw; idx += NTHREADS) {
-    const int c = idx / rows, r = idx - (idx / rows) * rows;
-    Cb[idx] = ldg(C + r + (size_t)(c0 + c) * ldc);
-  }
-  if (TS)
-    for (int idx = tid; idx < nref * cw; idx += NTHREADS) {
-      const int c = idx / nref, r = idx - (idx / nref) * nref;
-      Ct[idx] = ldg(Ctop + r + (size_t)(c0 + c) * ldct);
+  if (!vt_staged) narrow_stage_vt<S, TS>(V, ldv, T, ldt, nref, IB, rows, sm, tri);
+  // the task's rows of C -- bottom tile (rows x cw) and, TS, top rows
+  // (nref x cw) -- in one batch of loads
+  {
+    const int nbot = rows * cw, ntot = nbot + (TS ? nref * cw : 0);
+    for (int base = tid; base < ntot; base += 4 * NTHREADS) {
+      S v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * NTHREADS;
+        v[u] = S(0);
+        if (idx < nbot) {
+          const int c = idx / rows, r = idx - c * rows;
+          v[u] = __ldcg(C + r + (size_t)(c0 + c) * ldc);
+        } else if (idx < ntot) {
+          const int e = idx - nbot, c = e / nref, r = e - c * nref;
+          v[u] = __ldcg(Ctop + r + (size_t)(c0 + c) * ldct);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * NTHREADS;
+        if (idx < nbot) Cb[idx] = v[u];
+        else if (idx < ntot) Ct[idx - nbot] = v[u];
+      }
     }
+  }
   __syncthreads();
   const int nblk = (nref + IB - 1) / IB;
   for (int bi = 0; bi < nblk; ++bi) {
@@ -415,7 +508,17 @@ __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restri
         const int pp = o / cw, c = o - (o / cw) * cw;
         const S* vcol = Vs + (size_t)(l0 + pp) * rows;
         const S* ccol = Cb + (size_t)c * rows;
-        for (int r = r0 + part; r < rows; r += tpo) acc = fma(vcol[r], ccol[r], acc);
+        // four independent partial sums (rows r, r+tpo, r+2tpo, r+3tpo)
+        S a1 = S(0), a2 = S(0), a3 = S(0);
+        int r = r0 + part;
+        for (; r + 3 * tpo < rows; r += 4 * tpo) {
+          acc = fma(vcol[r], ccol[r], acc);
+          a1 = fma(vcol[r + tpo], ccol[r + tpo], a1);
+          a2 = fma(vcol[r + 2 * tpo], ccol[r + 2 * tpo], a2);
+          a3 = fma(vcol[r + 3 * tpo], ccol[r + 3 * tpo], a3);
+        }
+        for (; r < rows; r += tpo) acc = fma(vcol[r], ccol[r], acc);
+        acc = (acc + a1) + (a2 + a3);
       }
       for (int off = tpo / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
       if (o < nout && part == 0) {
@@ -438,20 +541,29 @@ __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restri
         for (int q = po; q < ib; ++q) wv = fma(Tb[po + q * IB], Ws[q * cw + co], wv);
       }
     }
-    __syncthreads();
-    if (po >= 0) Ws[po * cw + co] = wv;
+    if (po >= 0) W2[po * cw + co] = wv;  // a second buffer: no barrier between the reads of Ws and this write
     __syncthreads();
     // phase C: Ctop(l0+p) -= W (TS); Cb(r) -= sum_p V(r, l0+p) W(p)
     if (TS)
       for (int o = tid; o < nout; o += NTHREADS) {
         const int pp = o / cw, c = o - (o / cw) * cw;
-        Ct[(l0 + pp) + (size_t)c * nref] -= Ws[pp * cw + c];
+        Ct[(l0 + pp) + (size_t)c * nref] -= W2[pp * cw + c];
       }
-    for (int o = tid; o < (rows - r0) * cw; o += NTHREADS) {
-      const int c = o / (rows - r0), r = r0 + (o - (o / (rows - r0)) * (rows - r0));
+    // two outputs per thread interleaved (independent chains)
+    const int nrr = rows - r0, nco = nrr * cw;
+    for (int o = tid; o < nco; o += 2 * NTHREADS) {
+      const int o2 = o + NTHREADS;
+      const bool two = o2 < nco;
+      const int c = o / nrr, r = r0 + (o - c * nrr);
+      const int c2 = two ? o2 / nrr : c, r2 = two ? r0 + (o2 - c2 * nrr) : r;
       S acc = Cb[r + (size_t)c * rows];
-      for (int pp = 0; pp < ib; ++pp) acc = fma(-Vs[r + (size_t)(l0 + pp) * rows], Ws[pp * cw + c], acc);
+      S acc2 = Cb[r2 + (size_t)c2 * rows];
+      for (int pp = 0; pp < ib; ++pp) {
+        acc = fma(-Vs[r + (size_t)(l0 + pp) * rows], W2[pp * cw + c], acc);
+        acc2 = fma(-Vs[r2 + (size_t)(l0 + pp) * rows], W2[pp * cw + c2], acc2);
+      }
       Cb[r + (size_t)c * rows] = acc;
+      if (two) Cb[r2 + (size_t)c2 * rows] = acc2;
     }
     __syncthreads();
   }
@@ -616,10 +728,7 @@ __device__ void geqrt(S* A, int lda, int rows, int cols, int IB, S* T, const Sme
       const int nr = rows - s0;
       S* P = sm.part;  // nr x w, ld nr
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nr * w; idx += NTHREADS) {
-        const int cc = idx / nr, r = idx - cc * nr;
-        P[idx] = ldg(A + (s0 + r) + (size_t)(s0 + cc) * lda);
-      }
+      stage_block<8>(P, nr, A + s0 + (size_t)s0 * lda, lda, nr, w, AllRd(), Ident());
       __syncthreads();
       panel_l2<S, false>(P, nr, nr, w, nullptr, 0, sm.tau + (s0 - l0), sm.red, bad);
       const bool whole = (w == ib);
@@ -672,14 +781,9 @@ __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, 
       const int nr = tri ? min(rows, s0 + w) : rows;  // rows of B this sub-panel reaches
       S* P = sm.part;  // nr x w
       __syncthreads();
-      for (int idx = threadIdx.x; idx < nr * w; idx += NTHREADS) {
-        const int cc = idx / nr, r = idx - cc * nr;
-        P[idx] = (tri && r > s0 + cc) ? S(0) : ldg(B + r + (size_t)(s0 + cc) * ldb);
-      }
-      for (int idx = threadIdx.x; idx < w * w; idx += NTHREADS) {
-        const int cc = idx / w, r = idx - cc * w;
-        sm.rs[idx] = (r <= cc) ? ldg(R + (s0 + r) + (size_t)(s0 + cc) * ldr) : S(0);
-      }
+      stage_block<8>(P, nr, B + (size_t)s0 * ldb, ldb, nr, w, [tri, s0](int r, int c) { return !(tri && r > s0 + c); },
+                     Ident());
+      stage_block<4>(sm.rs, w, R + s0 + (size_t)s0 * ldr, ldr, w, w, [](int r, int c) { return r <= c; }, Ident());
       __syncthreads();
       panel_l2<S, true>(P, nr, nr, w, sm.rs, w, sm.tau + (s0 - l0), sm.red, bad, tri ? s0 : -1);
       const bool whole = (w == ib);

@@ -236,6 +236,19 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_apply(ApplyArgs<S> a) 
     int type, sch, i, j, k;
     decode_task(a.tasks[t], type, sch, i, j, k);
     const int c0 = (int)((int64_t)sch * a.nrhs / Sp), c1 = (int)((int64_t)(sch + 1) * a.nrhs / Sp);
+    S* Ck = a.C + (size_t)k * NB;
+    const int ck = cols_of(k);
+    const int rw = type == TASK_UNMQR ? rows_of(k) : rows_of(i);
+    // few right-hand sides: stage the whole task in shared memory once; the
+    // reflectors and T are final (written by the factorization), so they are
+    // staged before the wait for the task's rows of C
+    const bool nar = narrow_fits(rw, ck, a.IB, c1 - c0);
+    if (nar) {
+      if (type == TASK_UNMQR)
+        narrow_stage_vt<S, false>(tileA(k, k), (int)a.lda, tfac(k, k), a.IB, ck, a.IB, rw, sm);
+      else
+        narrow_stage_vt<S, true>(tileA(i, k), (int)a.lda, tfac(i, k), a.IB, ck, a.IB, rw, sm);
+    }
     if (threadIdx.x == 0) {
       bool ok;
       const uint64_t to = a.timeout_ns;
@@ -250,27 +263,26 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_apply(ApplyArgs<S> a) 
     }
     __syncthreads();
     if (!s_ok) break;
-    S* Ck = a.C + (size_t)k * NB;
-    const int ck = cols_of(k);
-    // few right-hand sides: stage the whole task in shared memory once
     if (type == TASK_UNMQR) {
-      if (narrow_fits(rows_of(k), ck, a.IB, c1 - c0))
+      if (nar)
         apply_narrow<S, false, TR>(tileA(k, k), (int)a.lda, tfac(k, k), a.IB, ck, a.IB, nullptr, 0, Ck, (int)a.ldc,
-                                   rows_of(k), c0, c1, sm);
+                                   rows_of(k), c0, c1, sm, false, true);
       else
         apply_qt<S, false, TR>(tileA(k, k), (int)a.lda, tfac(k, k), a.IB, false, 0, ck, a.IB, nullptr, 0, Ck,
                                (int)a.ldc, rows_of(k), c0, c1, sm);
     } else {
-      if (narrow_fits(rows_of(i), ck, a.IB, c1 - c0))
+      if (nar)
         apply_narrow<S, true, TR>(tileA(i, k), (int)a.lda, tfac(i, k), a.IB, ck, a.IB, Ck, (int)a.ldc,
-                                  a.C + (size_t)i * NB, (int)a.ldc, rows_of(i), c0, c1, sm);
+                                  a.C + (size_t)i * NB, (int)a.ldc, rows_of(i), c0, c1, sm, false, true);
       else
         apply_qt<S, true, TR>(tileA(i, k), (int)a.lda, tfac(i, k), a.IB, false, 0, ck, a.IB, Ck, (int)a.ldc,
                               a.C + (size_t)i * NB, (int)a.ldc, rows_of(i), c0, c1, sm);
     }
-    __threadfence();
+    // publish: the barrier orders every thread's C writes before thread
+    // 0's fence and release (cumulative), one fence per task
     __syncthreads();
     if (threadIdx.x == 0) {
+      __threadfence();
       red_release_add(ctr(k, sch), 1u);
       if (type == TASK_TSMQR) red_release_add(ctr(i, sch), 1u);
     }

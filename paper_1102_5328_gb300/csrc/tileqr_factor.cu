@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -33,6 +34,8 @@ namespace {
 
 std::mutex g_mu;
 int64_t g_wait_timeout_us = 20LL * 1000 * 1000;
+std::atomic<void*> g_trace{nullptr};
+std::atomic<int64_t> g_trace_cap{0};
 int g_ctas_per_sm = 0;
 int g_split = 0;
 int g_order = 1;  // ticket order of the flat tree: 0 earliest start time, 1 list schedule
@@ -232,6 +235,8 @@ struct FactorArgs {
   unsigned* cnt;
   DevCtl* ctl;
   uint64_t timeout_ns;
+  TraceRec* trace;
+  int64_t trace_cap;
 };
 
 template <typename S>
@@ -258,7 +263,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr(FactorArgs<S> a) {
     if (t < 0 || t >= a.ntasks) break;
     int type, sch, i, j, k;
     decode_task(a.tasks[t], type, sch, i, j, k);
+    uint64_t t_take = 0, t_ready = 0;
     if (threadIdx.x == 0) {
+      if (a.trace) t_take = globaltimer();
       bool ok = true;
       const uint64_t to = a.timeout_ns;
       switch (type) {
@@ -278,6 +285,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr(FactorArgs<S> a) {
           break;
       }
       s_ok = ok;
+      if (a.trace) t_ready = globaltimer();
     }
     __syncthreads();
     if (!s_ok) break;
@@ -321,6 +329,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr(FactorArgs<S> a) {
           red_release_add(ctr(i, j, sch), 1u);
           break;
       }
+      trace_put(a.trace, a.trace_cap, t, type, t_take, t_ready);
     }
   }
 }
@@ -398,6 +407,7 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
   fa.W = W; fa.T = T; fa.m = m; fa.n = n; fa.NB = nb; fa.IB = ib; fa.MT = L.MT; fa.NT = L.NT; fa.S_ = L.S;
   fa.tasks = dtasks; fa.ntasks = ntasks; fa.cnt = cnt; fa.ctl = ctl;
   fa.timeout_ns = (uint64_t)g_wait_timeout_us * 1000ull;
+  fa.trace = (TraceRec*)g_trace.load(); fa.trace_cap = g_trace_cap.load();
   if (g_record) {
     if (!g_ev[0]) {
       if ((e = cudaEventCreate(&g_ev[0])) != cudaSuccess) return (int)e;
@@ -496,6 +506,7 @@ int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, in
   fa.W = W; fa.T = T; fa.m = m; fa.n = n; fa.NB = nb; fa.IB = ib; fa.MT = L.MT; fa.NT = L.NT; fa.S_ = L.S;
   fa.tasks = dtasks; fa.ntasks = L.ntasks; fa.cnt = cnt; fa.ctl = ctl;
   fa.timeout_ns = (uint64_t)g_wait_timeout_us * 1000ull;
+  fa.trace = (TraceRec*)g_trace.load(); fa.trace_cap = g_trace_cap.load();
   persistent_qr<double><<<grid, NTHREADS, smem_elems<double>() * sizeof(double), st>>>(fa);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   tiles_to_cm<double><<<1184, 256, 0, st>>>(W, A, lda, m, n, nb, L.MT);
@@ -519,6 +530,11 @@ int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib) {
 }
 
 // ---------------------------------------------------------------------------
+void qr_trace_target(void** buf, int64_t* cap) {
+  *buf = g_trace.load();
+  *cap = g_trace_cap.load();
+}
+
 extern "C" {
 
 int qr_workspace(int64_t m, int64_t n, int nb, int ib, int prec, int64_t* t_elems, int64_t* scratch_bytes) {
@@ -568,6 +584,14 @@ int qr_status(const void* scratch, int* status, void* stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return (int)e;
   *status = h.status;
+  return 0;
+}
+
+int qr_set_trace(void* d_buf, int64_t capacity) {
+  if (capacity < 0) return -2;
+  if (d_buf && ((uintptr_t)d_buf & 31)) return -1;
+  g_trace_cap.store(d_buf ? capacity : 0);
+  g_trace.store(d_buf);
   return 0;
 }
 

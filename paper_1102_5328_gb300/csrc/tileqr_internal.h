@@ -31,3 +31,7 @@ int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib, int*
 // Builds (and caches) the host task order for this shape so that a later
 // timed qr_factor_* call does not include it. Returns 0 on success.
 int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib);
+
+// The trace buffer set by qr_set_trace (null when tracing is off) and its
+// capacity in records; read at each launch of a persistent kernel.
+void qr_trace_target(void** buf, int64_t* cap);

@@ -18,6 +18,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "sched.cuh"
 #include "tileqr_internal.h"
 
 namespace {
@@ -32,59 +33,127 @@ __global__ void cvt(int64_t m, int64_t n, const Src* s, int64_t lds, Dst* d, int
   }
 }
 
-// Triangular solve with the n x n upper triangle of R (ld ldr), one CTA per
-// right-hand side, in place on X (ld ldx). trans = 0: R x = y (backward);
-// trans = 1: R^T x = y (forward). Blocks of 32 rows: one warp solves the
-// diagonal block, then the whole CTA updates the remaining rows.
+// Triangular solve with the n x n upper triangle of R (ld ldr), in place on
+// the nk <= 8 columns of X (ld ldx). trans = 0: R x = y (backward
+// substitution); trans = 1: R^T x = y (forward substitution).
+//
+// Wavefront over row blocks of TRSM_BS rows: the blocks are taken in solve
+// order s (backward: last block first) from an atomic ticket, so the smallest
+// unfinished s is always held by a running CTA and the waits end (no
+// co-residency is assumed). The CTA holding s subtracts the contribution of
+// every earlier-solved block s' < s as soon as flag[s'] is set (one 64 x 64
+// block of R against 64 x nk solved values), then solves its diagonal block
+// (one warp per right-hand side) and publishes flag[s]. Waits are bounded
+// (status bit and abort flag in ctl, as in the factorization's scheduler).
+constexpr int TRSM_BS = 64;
+constexpr int TRSM_LD = TRSM_BS + 1;  // padded column stride of the staged block
+
 template <typename S>
-__global__ void trsm_upper(int n, const S* __restrict__ R, int64_t ldr, S* X, int64_t ldx, int trans) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  S* ys = reinterpret_cast<S*>(smraw);
-  S* x = X + (size_t)blockIdx.x * ldx;
-  for (int i = threadIdx.x; i < n; i += TB) ys[i] = x[i];
-  __syncthreads();
-  const int nblk = (n + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  for (int bb = 0; bb < nblk; ++bb) {
-    const int b = trans ? bb : nblk - 1 - bb;
-    const int i0 = b * 32, bs = min(32, n - i0);
-    if (threadIdx.x < 32) {
-      S y = lane < bs ? ys[i0 + lane] : S(0);
-      if (!trans) {
-        for (int j = bs - 1; j >= 0; --j) {
-          S xj = __shfl_sync(0xffffffffu, y, j);
-          xj = xj / R[(i0 + j) + (size_t)(i0 + j) * ldr];
-          if (lane == j) y = xj;
-          if (lane < j) y -= R[(i0 + lane) + (size_t)(i0 + j) * ldr] * xj;
-        }
-      } else {
-        for (int j = 0; j < bs; ++j) {
-          S xj = __shfl_sync(0xffffffffu, y, j);
-          xj = xj / R[(i0 + j) + (size_t)(i0 + j) * ldr];
-          if (lane == j) y = xj;
-          if (lane > j && lane < bs) y -= R[(i0 + j) + (size_t)(i0 + lane) * ldr] * xj;
-        }
-      }
-      if (lane < bs) ys[i0 + lane] = y;
-    }
-    __syncthreads();
-    if (!trans) {
-      for (int r = threadIdx.x; r < i0; r += TB) {
-        S acc = S(0);
-        for (int j = 0; j < bs; ++j) acc = fma(R[r + (size_t)(i0 + j) * ldr], ys[i0 + j], acc);
-        ys[r] -= acc;
-      }
-    } else {
-      for (int r = i0 + bs + threadIdx.x; r < n; r += TB) {
-        S acc = S(0);
-        const S* rc = R + (size_t)r * ldr + i0;
-        for (int j = 0; j < bs; ++j) acc = fma(rc[j], ys[i0 + j], acc);
-        ys[r] -= acc;
+__global__ void __launch_bounds__(TB) trsm_wave(int n, const S* __restrict__ R, int64_t ldr, S* X, int64_t ldx,
+                                                int nk, int trans, tqr::DevCtl* ctl, unsigned* flags,
+                                                uint64_t timeout_ns) {
+  __shared__ S Rb[TRSM_BS * TRSM_LD];  // Rb[c * TRSM_LD + r] = coefficient of x_c in equation r
+  __shared__ S xs[TRSM_BS * 8];        // solved values of a dependency block, [c * 8 + k]
+  __shared__ S ys[TRSM_BS * 8];        // right-hand side of the own block, [r * 8 + k]
+  __shared__ int s_s, s_ok;
+  const int nbk = (n + TRSM_BS - 1) / TRSM_BS;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int r = tid & (TRSM_BS - 1), kg = tid >> 6;  // output rows r, columns kg and kg + 4
+  // stage the block of coefficients of the variables of row block bc in the
+  // equations of row block br (Rb as above; zero outside the matrix)
+  auto stage = [&](int br, int bc) {
+    const int rr0 = br * TRSM_BS, cc0 = bc * TRSM_BS;
+    const int nr = min(TRSM_BS, n - rr0), nc = min(TRSM_BS, n - cc0);
+    for (int idx = tid; idx < TRSM_BS * TRSM_BS; idx += TB) {
+      const int i = idx & (TRSM_BS - 1), j = idx / TRSM_BS;
+      S v = S(0);
+      if (trans == 0) {  // equation rr0+i, variable cc0+j: R(rr0+i, cc0+j)
+        if (i < nr && j < nc) v = R[(rr0 + i) + (size_t)(cc0 + j) * ldr];
+        Rb[j * TRSM_LD + i] = v;
+      } else {           // equation rr0+j, variable cc0+i: R^T(rr0+j, cc0+i) = R(cc0+i, rr0+j)
+        if (i < nc && j < nr) v = R[(cc0 + i) + (size_t)(rr0 + j) * ldr];
+        Rb[i * TRSM_LD + j] = v;
       }
     }
+  };
+  for (;;) {
+    if (tid == 0) {
+      int sv = -1;
+      if (!((volatile int*)&ctl->abort)[0]) sv = (int)atomicAdd(&ctl->ticket, 1u);
+      s_s = sv;
+    }
     __syncthreads();
+    const int sidx = s_s;
+    if (sidx < 0 || sidx >= nbk) break;
+    const int b = trans ? sidx : nbk - 1 - sidx;
+    const int r0 = b * TRSM_BS, nr = min(TRSM_BS, n - r0);
+    S acc0 = (r < nr && kg < nk) ? X[(r0 + r) + (size_t)kg * ldx] : S(0);
+    S acc1 = (r < nr && kg + 4 < nk) ? X[(r0 + r) + (size_t)(kg + 4) * ldx] : S(0);
+    bool ok = true;
+    for (int sp = 0; sp < sidx && ok; ++sp) {
+      const int bp = trans ? sp : nbk - 1 - sp;
+      const int c0 = bp * TRSM_BS, nc = min(TRSM_BS, n - c0);
+      stage(b, bp);  // R does not change: staged before the wait
+      if (tid == 0) s_ok = tqr::wait_ge(flags + sp, 1, 1u, ctl, timeout_ns);
+      __syncthreads();
+      ok = s_ok;
+      if (ok) {
+        for (int idx = tid; idx < TRSM_BS * 8; idx += TB) {
+          const int c = idx >> 3, k = idx & 7;
+          xs[idx] = (c < nc && k < nk) ? __ldcg(X + (c0 + c) + (size_t)k * ldx) : S(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int c = 0; c < TRSM_BS; ++c) {
+          const S a = Rb[c * TRSM_LD + r];
+          acc0 = fma(-a, xs[c * 8 + kg], acc0);
+          acc1 = fma(-a, xs[c * 8 + kg + 4], acc1);
+        }
+      }
+      __syncthreads();
+    }
+    if (!ok) break;
+    // diagonal block: one warp per right-hand side, lane holds rows lane, lane+32
+    stage(b, b);
+    ys[r * 8 + kg] = acc0;
+    ys[r * 8 + kg + 4] = acc1;
+    __syncthreads();
+    if (wid < nk) {
+      const int k = wid;
+      S y0 = ys[lane * 8 + k], y1 = ys[(lane + 32) * 8 + k];
+      for (int t = 0; t < nr; ++t) {
+        const int j = trans ? t : nr - 1 - t;
+        const S v = __shfl_sync(0xffffffffu, j < 32 ? y0 : y1, j & 31);
+        const S xj = v / Rb[j * TRSM_LD + j];
+        const S a0 = Rb[j * TRSM_LD + lane], a1 = Rb[j * TRSM_LD + lane + 32];
+        if (trans) {
+          if (lane > j) y0 = fma(-a0, xj, y0);
+          if (lane + 32 > j) y1 = fma(-a1, xj, y1);
+        } else {
+          if (lane < j) y0 = fma(-a0, xj, y0);
+          if (lane + 32 < j) y1 = fma(-a1, xj, y1);
+        }
+        if (lane == (j & 31)) {
+          if (j < 32) y0 = xj;
+          else y1 = xj;
+        }
+      }
+      ys[lane * 8 + k] = y0;
+      ys[(lane + 32) * 8 + k] = y1;
+    }
+    __syncthreads();
+    if (r < nr) {
+      if (kg < nk) __stcg(X + (r0 + r) + (size_t)kg * ldx, ys[r * 8 + kg]);
+      if (kg + 4 < nk) __stcg(X + (r0 + r) + (size_t)(kg + 4) * ldx, ys[r * 8 + kg + 4]);
+    }
+    // publish: the barrier orders every thread's writes of x before
+    // thread 0's fence and release (cumulative), one fence per block
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      tqr::red_release_add(flags + sidx, 1u);
+    }
   }
-  for (int i = threadIdx.x; i < n; i += TB) x[i] = ys[i];
 }
 
 // Partial products P[s][row][k] = sum_{c in split s} A(row, c) x(c, k) for
@@ -243,7 +312,7 @@ __global__ void accumulate(int64_t rows, int nk, const S* v, int64_t ldv, const 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct SolveLayout {
-  size_t a, t, scr, ap, bw, hw, tw, x, r, f, g, p, q, scale, sq, total;
+  size_t a, t, scr, ap, bw, hw, tw, x, r, f, g, p, q, scale, sq, tsync, total;
   int64_t apbytes;
   int64_t t_el, sbytes;
   int nsplit, nrb, rpb;
@@ -285,6 +354,7 @@ SolveLayout solve_layout(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, i
   L.q = off; off = al(off + (size_t)L.nrb * n * 8 * 8);
   L.scale = off; off = al(off + 2 * 8 * 8);
   L.sq = off; off = al(off + 2 * 8 * 8);
+  L.tsync = off; off = al(off + 64 + (size_t)((n + TRSM_BS - 1) / TRSM_BS) * 4);
   L.total = off;
   return L;
 }
@@ -310,13 +380,22 @@ int residuals(int64_t m, int64_t n, int nk, const double* A, int64_t lda, const 
   return e == cudaSuccess ? 0 : (int)e;
 }
 
+// Wavefront triangular solve (trsm_wave). sync: the solve's control block
+// (tqr::DevCtl, 64 bytes) followed by one flag per row block. Ticket and
+// flags are cleared here on the stream; the status and abort words persist
+// over the solve and are cleared once at its start.
 template <typename S>
-int trsm(int64_t n, const S* R, int64_t ldr, S* X, int64_t ldx, int nk, int trans, cudaStream_t st) {
-  const size_t smem = (size_t)n * sizeof(S);
-  if (smem > 200 * 1024) return -1;
-  cudaError_t e = cudaFuncSetAttribute(trsm_upper<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int trsm(int64_t n, const S* R, int64_t ldr, S* X, int64_t ldx, int nk, int trans, char* sync, cudaStream_t st) {
+  const int nbk = (int)((n + TRSM_BS - 1) / TRSM_BS);
+  cudaError_t e = cudaMemsetAsync(sync + 8, 0, 56 + (size_t)nbk * 4, st);
   if (e != cudaSuccess) return (int)e;
-  trsm_upper<S><<<nk, TB, smem, st>>>((int)n, R, ldr, X, ldx, trans);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(nbk, 2 * sms));
+  const uint64_t timeout_ns = (uint64_t)qr_get_option(QR_OPT_WAIT_TIMEOUT_US) * 1000ull;
+  trsm_wave<S><<<grid, TB, 0, st>>>((int)n, R, ldr, X, ldx, nk, trans, (tqr::DevCtl*)sync, (unsigned*)(sync + 64),
+                                    timeout_ns);
   e = cudaGetLastError();
   return e == cudaSuccess ? 0 : (int)e;
 }
@@ -377,13 +456,13 @@ int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, cons
     scale_cvt<double, S><<<grid_for(m * nk), TB, 0, st>>>(m, nk, f, m, scale, Bw, m);
     scale_cvt<double, S><<<grid_for(n * nk), TB, 0, st>>>(n, nk, g, n, scale, Hw, n);
     // R^T h = g/s
-    if ((rc = trsm<S>(n, Af, m, Hw, n, nk, 1, st))) return rc;
+    if ((rc = trsm<S>(n, Af, m, Hw, n, nk, 1, w + L.tsync, st))) return rc;
     // d = Q^T f/s
     if ((rc = apply<S>(m, n, nk, Af, nb, ib, p, T, Bw, 1, w + L.ap, L.apbytes, st))) return rc;
     // Tw = d(0:n) - h ; Bw(0:n) = h
     split_correction<S><<<grid_for(n * nk), TB, 0, st>>>(m, n, nk, Bw, Hw, Tw);
     // R dx = Tw
-    if ((rc = trsm<S>(n, Af, m, Tw, n, nk, 0, st))) return rc;
+    if ((rc = trsm<S>(n, Af, m, Tw, n, nk, 0, w + L.tsync, st))) return rc;
     // dr = Q [h; d(n:m)]
     if ((rc = apply<S>(m, n, nk, Af, nb, ib, p, T, Bw, 0, w + L.ap, L.apbytes, st))) return rc;
     if ((e = cudaMemsetAsync(sq, 0, 2 * 8 * 8, st)) != cudaSuccess) return (int)e;
@@ -470,6 +549,7 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda
   }
   if (rc) return rc;
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  if ((e = cudaMemsetAsync(w + L.tsync, 0, 64, st)) != cudaSuccess) return (int)e;
   int iters = 0, conv = 1;
   for (int64_t k0 = 0; k0 < nrhs; k0 += 8) {
     const int nk = (int)std::min<int64_t>(8, nrhs - k0);
@@ -483,9 +563,10 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda
   if (info) {
     info[0] = iters;
     info[1] = conv;
-    int status = 0;
+    int status = 0, tstatus = 0;
     if ((rc = qr_status(w + L.scr, &status, st)) != 0) return rc;
-    info[2] = status;
+    if ((rc = qr_status(w + L.tsync, &tstatus, st)) != 0) return rc;
+    info[2] = status | tstatus;
   }
   return 0;
 }

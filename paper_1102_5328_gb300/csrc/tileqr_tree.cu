@@ -367,6 +367,8 @@ struct DagArgs {
   unsigned* cnt;
   DevCtl* ctl;
   uint64_t timeout_ns;
+  TraceRec* trace;
+  int64_t trace_cap;
 };
 
 template <typename S>
@@ -396,7 +398,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr_dag(DagArgs<S> a) {
     if (tk < 0 || tk >= a.ntasks) break;
     const TaskRec t = s_task;
     const int type = t.type, i = t.i, h = t.h, j = t.j, k = t.k, sc = t.s;
+    uint64_t t_take = 0, t_ready = 0;
     if (threadIdx.x == 0) {
+      if (a.trace) t_take = globaltimer();
       bool ok = true;
       const uint64_t to = a.timeout_ns;
       switch (type) {
@@ -414,6 +418,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr_dag(DagArgs<S> a) {
           break;
       }
       s_ok = ok;
+      if (a.trace) t_ready = globaltimer();
     }
     __syncthreads();
     if (!s_ok) break;
@@ -460,6 +465,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr_dag(DagArgs<S> a) {
           red_release_add(ctr(i, j, sc), 1u);
           break;
       }
+      trace_put(a.trace, a.trace_cap, tk, type, t_take, t_ready);
     }
   }
 }
@@ -514,6 +520,13 @@ int factor_p_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, int p
   da.MT = L.MT; da.NT = L.NT; da.S_ = L.S; da.tasks = (const TaskRec*)(base + L.off_tasks);
   da.ntasks = (int64_t)dag.tasks.size(); da.cnt = (unsigned*)(base + L.off_cnt); da.ctl = (DevCtl*)base;
   da.timeout_ns = (uint64_t)qr_get_option(QR_OPT_WAIT_TIMEOUT_US) * 1000ull;
+  {
+    void* tb = nullptr;
+    int64_t tc = 0;
+    qr_trace_target(&tb, &tc);
+    da.trace = (TraceRec*)tb;
+    da.trace_cap = tc;
+  }
   persistent_qr_dag<S><<<grid, NTHREADS, smem, st>>>(da);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   tiles_to_cm<S><<<1184, 256, 0, st>>>(W, A, lda, m, n, nb, L.MT);
@@ -538,6 +551,8 @@ struct ApplyDagArgs {
   unsigned* cnt;
   DevCtl* ctl;
   uint64_t timeout_ns;
+  TraceRec* trace;
+  int64_t trace_cap;
 };
 
 __global__ void zero_u32(unsigned* p, int64_t n) {
@@ -571,41 +586,55 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_apply_dag(ApplyDagArgs
     if (tk < 0 || tk >= a.ntasks) break;
     const TaskRec t = s_task;
     const int type = t.type, i = t.i, h = t.h, k = t.k, sc = t.s;
+    uint64_t t_take = 0, t_ready = 0;
+    if (threadIdx.x == 0 && a.trace) t_take = globaltimer();
+    const int c0 = (int)((int64_t)sc * a.nrhs / Sp), c1 = (int)((int64_t)(sc + 1) * a.nrhs / Sp);
+    const int ck = cols_of(k);
+    S* Ch = a.C + (size_t)h * NB;
+    // few right-hand sides: stage the whole task in shared memory once; the
+    // reflectors and T are final (written by the factorization), so they are
+    // staged before the wait for the task's rows of C
+    const int rw = type == D_UNMQR ? rows_of(h) : (type == D_TSMQR ? rows_of(i) : min(rows_of(i), ck));
+    const bool nar = narrow_fits(rw, ck, a.IB, c1 - c0);
+    const S* tf = type == D_UNMQR ? t1(h, k) : (type == D_TSMQR ? t1(i, k) : t2(i, k));
+    if (nar) {
+      if (type == D_UNMQR)
+        narrow_stage_vt<S, false>(tileA(h, k), (int)a.lda, tf, a.IB, ck, a.IB, rw, sm);
+      else
+        narrow_stage_vt<S, true>(tileA(i, k), (int)a.lda, tf, a.IB, ck, a.IB, rw, sm, type == D_TTMQR);
+    }
     if (threadIdx.x == 0) {
       bool ok = wait_ge(ctr(h, sc), 1, t.ctop, a.ctl, a.timeout_ns);
       if (ok && type != D_UNMQR) ok = wait_ge(ctr(i, sc), 1, t.cbot, a.ctl, a.timeout_ns);
       s_ok = ok;
+      if (a.trace) t_ready = globaltimer();
     }
     __syncthreads();
     if (!s_ok) break;
-    const int c0 = (int)((int64_t)sc * a.nrhs / Sp), c1 = (int)((int64_t)(sc + 1) * a.nrhs / Sp);
-    const int ck = cols_of(k);
-    S* Ch = a.C + (size_t)h * NB;
-    // few right-hand sides: stage the whole task in shared memory once
-    const int rw = type == D_UNMQR ? rows_of(h) : (type == D_TSMQR ? rows_of(i) : min(rows_of(i), ck));
-    const bool nar = narrow_fits(rw, ck, a.IB, c1 - c0);
     if (type == D_UNMQR) {
       if (nar)
         apply_narrow<S, false, TR>(tileA(h, k), (int)a.lda, t1(h, k), a.IB, ck, a.IB, nullptr, 0, Ch, (int)a.ldc, rw,
-                                   c0, c1, sm);
+                                   c0, c1, sm, false, true);
       else
         apply_qt<S, false, TR>(tileA(h, k), (int)a.lda, t1(h, k), a.IB, false, 0, ck, a.IB, nullptr, 0, Ch,
                                (int)a.ldc, rw, c0, c1, sm);
     } else {
-      const S* tf = type == D_TSMQR ? t1(i, k) : t2(i, k);
       const bool tri = type == D_TTMQR;
       if (nar)
         apply_narrow<S, true, TR>(tileA(i, k), (int)a.lda, tf, a.IB, ck, a.IB, Ch, (int)a.ldc, a.C + (size_t)i * NB,
-                                  (int)a.ldc, rw, c0, c1, sm, tri);
+                                  (int)a.ldc, rw, c0, c1, sm, tri, true);
       else
         apply_qt<S, true, TR>(tileA(i, k), (int)a.lda, tf, a.IB, false, 0, ck, a.IB, Ch, (int)a.ldc,
                               a.C + (size_t)i * NB, (int)a.ldc, rw, c0, c1, sm, tri);
     }
-    __threadfence();
+    // publish: the barrier orders every thread's C writes before thread
+    // 0's fence and release (cumulative), one fence per task
     __syncthreads();
     if (threadIdx.x == 0) {
+      __threadfence();
       red_release_add(ctr(h, sc), 1u);
       if (type != D_UNMQR) red_release_add(ctr(i, sc), 1u);
+      trace_put(a.trace, a.trace_cap, tk, type, t_take, t_ready);
     }
   }
 }
@@ -688,6 +717,13 @@ int apply_p_impl(int64_t m, int64_t n, int64_t nrhs, const S* A, int64_t lda, in
   aa.tasks = (const TaskRec*)(base + L.off_tasks); aa.ntasks = (int64_t)dag.tasks.size();
   aa.cnt = (unsigned*)(base + L.off_cnt); aa.ctl = (DevCtl*)base;
   aa.timeout_ns = (uint64_t)qr_get_option(QR_OPT_WAIT_TIMEOUT_US) * 1000ull;
+  {
+    void* tb = nullptr;
+    int64_t tc = 0;
+    qr_trace_target(&tb, &tc);
+    aa.trace = (TraceRec*)tb;
+    aa.trace_cap = tc;
+  }
   return trans ? launch_apply_dag<S, true>(aa, st) : launch_apply_dag<S, false>(aa, st);
 }
 

@@ -198,3 +198,24 @@ def test_narrow_application_matches_wide(q, nrhs):
         q.qr_apply_qt(f, C1, trans=trans, parallel=False)
         q.qr_apply_qt(f, C2, trans=trans, parallel=True)
         assert torch.allclose(C1, C2, rtol=0, atol=100 * n * U * float(C1.abs().max()))
+
+
+def test_task_trace(q):
+    """qr_set_trace: one record per task of the persistent factorization,
+    timestamps ordered, SM ids within the device, tracing off afterwards."""
+    m, n, nb, ib = 700, 500, 64, 16
+    A = torch.from_numpy(np.ascontiguousarray(inputs.uniform_matrix(m, n, seed=3).T)).cuda().t()
+    ntasks = q.lib().qr_task_count(m, n, nb, ib)
+    buf = torch.full((ntasks + 8, 4), -1, dtype=torch.int64, device="cuda")
+    q.qr_set_trace(buf)
+    try:
+        q.qr_factor(A, nb, ib)
+        torch.cuda.synchronize()
+    finally:
+        q.qr_set_trace(None)
+    task, typ, sm, t_take, t_ready, t_done = q.read_trace(buf, ntasks)
+    assert sorted(task.tolist()) == list(range(ntasks))
+    assert set(typ.tolist()) == {0, 1, 2, 3}
+    assert np.all(t_take <= t_ready) and np.all(t_ready <= t_done)
+    assert sm.max() < torch.cuda.get_device_properties(0).multi_processor_count
+    assert np.all(buf[ntasks:].cpu().numpy() == -1)

@@ -78,3 +78,19 @@ def test_normal_equations_residual(q):
     ne = _normal_eq(A, B, X.cpu().numpy())
     ne_ref = _normal_eq(A, B, Xref)
     assert np.all(ne <= 4 * ne_ref + 10 * kappa * U), (ne, ne_ref)
+
+
+@pytest.mark.parametrize("m,n,nrhs,p", [(100, 40, 1, 1), (700, 130, 10, 1), (3000, 1100, 9, 4), (5000, 64, 3, 8)])
+def test_plain_solve_shapes(q, m, n, nrhs, p):
+    """Plain FP64 solve against the oracle's QR solve: one row block of the
+    triangular solves (n < 64), ragged last blocks (130 = 2 x 64 + 2,
+    1100 = 17 x 64 + 12), an exact multiple, and several groups of <= 8
+    right-hand sides."""
+    A = inputs.uniform_matrix(m, n, seed=m + n)
+    B = inputs.normal_matrix(m, nrhs, seed=nrhs)
+    Xo = oracle.ls_solve(A, B)
+    X, info = q.qr_solve_ls(to_dev(A), to_dev(B), prec=q.QR_PREC_F64, nb=64, ib=8, p=p)
+    assert info[2] == 0
+    err = fwd_err(X.cpu().numpy(), Xo)
+    kappa = np.linalg.cond(A)
+    assert np.all(err < 1e3 * n * U * kappa * (1 + kappa)), err
