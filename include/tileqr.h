@@ -51,6 +51,8 @@ extern "C" {
 #define QR_OPT_DROP_TASK       5 /* test hook: omit this ticket from the task list (-1 = off) */
 #define QR_OPT_RECORD_EVENTS   6 /* 1: bracket each persistent kernel with CUDA events on its stream */
 #define QR_OPT_ORDER           7 /* flat-tree ticket order: 0 earliest start time, 1 list schedule (default) */
+#define QR_OPT_PANEL_WEIGHT    8 /* list schedule: GEQRT/TSQRT cost as a percentage of their flops (default 150) */
+#define QR_OPT_UNMQR_WEIGHT    9 /* list schedule: UNMQR cost as a percentage of its flops (default 100) */
 
 /*
  * qr_workspace -- sizes of the caller-owned buffers of qr_factor_*.
@@ -185,6 +187,17 @@ int qr_factor_d_noalloc(int64_t m, int64_t n, double *d_A, int64_t lda, int nb, 
  * the factorization that last used d_scratch into *status (QR_DEV_* bits).
  */
 int qr_status(const void *d_scratch, int *status, void *stream);
+
+/*
+ * qr_set_task_costs -- measured costs of the four task types (GEQRT, UNMQR,
+ * TSQRT, TSMQR: any time unit, e.g. median service times from qr_set_trace)
+ * for factorizations at precision prec with this (nb, ib). The host list
+ * schedule that orders the persistent kernel's tickets then uses them in
+ * place of its flop-count weights (QR_OPT_PANEL_WEIGHT, QR_OPT_UNMQR_WEIGHT).
+ * costs = NULL removes the entry. Returns -1..-3 for a bad prec, nb, ib and
+ * -4 for a cost that is not positive and finite.
+ */
+int qr_set_task_costs(int prec, int nb, int ib, const double *costs);
 
 /*
  * qr_set_trace -- per-task trace of the persistent factorization and Q

@@ -29,6 +29,8 @@ QR_OPT_GRID_LIMIT = 4
 QR_OPT_DROP_TASK = 5
 QR_OPT_RECORD_EVENTS = 6
 QR_OPT_ORDER = 7
+QR_OPT_PANEL_WEIGHT = 8
+QR_OPT_UNMQR_WEIGHT = 9
 
 
 _TUNED_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")
@@ -46,6 +48,15 @@ def lib():
             path = os.path.join(_TUNED_DIR, name)
             if os.path.exists(path):
                 L.qr_load_table(path.encode())
+        for name in ("gb300_fp64_costs.json", "gb300_fp32_costs.json"):
+            path = os.path.join(_TUNED_DIR, name)
+            if os.path.exists(path):
+                with open(path) as f:
+                    tab = json.load(f)
+                prec = QR_PREC_F32 if tab.get("prec") == "fp32" else QR_PREC_F64
+                for e in tab.get("entries", []):
+                    c = (ctypes.c_double * 4)(*e["costs"])
+                    L.qr_set_task_costs(prec, int(e["nb"]), int(e["ib"]), c)
         path = os.path.join(_TUNED_DIR, "gb300_batched_classes.json")
         if os.path.exists(path):
             with open(path) as f:
@@ -295,6 +306,13 @@ def qr_status(scratch, stream=None):
 
 def qr_set_option(opt, value):
     _lib.check(lib().qr_set_option(opt, int(value)), "qr_set_option")
+
+
+def qr_set_task_costs(dtype, nb, ib, costs=None):
+    """Measured (GEQRT, UNMQR, TSQRT, TSMQR) costs for the list schedule of
+    factorizations with this (nb, ib); None removes them."""
+    c = None if costs is None else (ctypes.c_double * 4)(*[float(v) for v in costs])
+    _lib.check(lib().qr_set_task_costs(_prec(dtype), nb, ib, c), "qr_set_task_costs")
 
 
 def qr_set_trace(buf=None):

@@ -49,6 +49,7 @@ SIGNATURES = [
                             c_int, c_dbl, ctypes.POINTER(c_int), c_vp, c_i64, c_vp]),
     ("qr_set_option", c_int, [c_int, c_i64]),
     ("qr_set_trace", c_int, [c_vp, c_i64]),
+    ("qr_set_task_costs", c_int, [c_int, c_int, c_int, ctypes.POINTER(c_dbl)]),
     ("qr_get_option", c_i64, [c_int]),
     ("qr_task_count", c_i64, [c_i64, c_i64, c_int, c_int]),
     ("qr_last_kernel_ms", c_int, [ctypes.POINTER(ctypes.c_float)]),

@@ -424,9 +424,9 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
 // costs three barriers. Same operations as apply_qt (blocks in order, W =
 // V^T C, W <- T^T W or T W, C -= V W), different summation order.
 // Usable when narrow_fits(): rows * nref <= VS_CAP, IB * nref <= PART_CAP,
-// (rows + nref) * cw <= W_CAP, IB * cw <= min(TS_CAP, NTHREADS), cw <= 16.
+// ((rows | 1) + nref) * cw <= W_CAP, IB * cw <= min(TS_CAP, NTHREADS), cw <= 16.
 __host__ __device__ inline bool narrow_fits(int rows, int nref, int IB, int cw) {
-  return rows * nref <= VS_CAP && IB * nref <= PART_CAP && (rows + nref) * cw <= W_CAP && IB * cw <= TS_CAP &&
+  return rows * nref <= VS_CAP && IB * nref <= PART_CAP && ((rows | 1) + nref) * cw <= W_CAP && IB * cw <= TS_CAP &&
          IB * cw <= NTHREADS && cw <= 16;
 }
 
@@ -457,8 +457,11 @@ __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restri
   if (cw <= 0 || nref <= 0 || rows <= 0) return;
   S* Vs = sm.vs;            // rows x nref, column-major (ld rows)
   S* Ts = sm.part;          // IB x nref (ld IB)
-  S* Cb = sm.w;             // rows x cw (ld rows): C (GE) or the bottom tile (TS)
-  S* Ct = sm.w + rows * cw; // nref x cw (ld nref): top rows (TS)
+  // C (GE) or the bottom tile (TS), rows x cw with an odd leading dimension
+  // so that the columns read together in phase A fall in different banks
+  const int ldb = rows | 1;
+  S* Cb = sm.w;             // rows x cw (ld ldb)
+  S* Ct = sm.w + ldb * cw;  // nref x cw (ld nref): top rows (TS)
   S* Ws = sm.ts;            // IB x cw
   S* W2 = sm.ts + NTHREADS; // IB x cw (IB * cw <= NTHREADS), T applied
   __syncthreads();
@@ -484,7 +487,10 @@ __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restri
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int idx = base + u * NTHREADS;
-        if (idx < nbot) Cb[idx] = v[u];
+        if (idx < nbot) {
+          const int c = idx / rows, r = idx - c * rows;
+          Cb[r + c * ldb] = v[u];
+        }
         else if (idx < ntot) Ct[idx - nbot] = v[u];
       }
     }
@@ -507,7 +513,7 @@ __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restri
       if (o < nout) {
         const int pp = o / cw, c = o - (o / cw) * cw;
         const S* vcol = Vs + (size_t)(l0 + pp) * rows;
-        const S* ccol = Cb + (size_t)c * rows;
+        const S* ccol = Cb + (size_t)c * ldb;
         // four independent partial sums (rows r, r+tpo, r+2tpo, r+3tpo)
         S a1 = S(0), a2 = S(0), a3 = S(0);
         int r = r0 + part;
@@ -556,20 +562,20 @@ __device__ void apply_narrow(const S* __restrict__ V, int ldv, const S* __restri
       const bool two = o2 < nco;
       const int c = o / nrr, r = r0 + (o - c * nrr);
       const int c2 = two ? o2 / nrr : c, r2 = two ? r0 + (o2 - c2 * nrr) : r;
-      S acc = Cb[r + (size_t)c * rows];
-      S acc2 = Cb[r2 + (size_t)c2 * rows];
+      S acc = Cb[r + (size_t)c * ldb];
+      S acc2 = Cb[r2 + (size_t)c2 * ldb];
       for (int pp = 0; pp < ib; ++pp) {
         acc = fma(-Vs[r + (size_t)(l0 + pp) * rows], W2[pp * cw + c], acc);
         acc2 = fma(-Vs[r2 + (size_t)(l0 + pp) * rows], W2[pp * cw + c2], acc2);
       }
-      Cb[r + (size_t)c * rows] = acc;
-      if (two) Cb[r2 + (size_t)c2 * rows] = acc2;
+      Cb[r + (size_t)c * ldb] = acc;
+      if (two) Cb[r2 + (size_t)c2 * ldb] = acc2;
     }
     __syncthreads();
   }
   for (int idx = tid; idx < rows * cw; idx += NTHREADS) {
     const int c = idx / rows, r = idx - (idx / rows) * rows;
-    stg(C + r + (size_t)(c0 + c) * ldc, Cb[idx]);
+    stg(C + r + (size_t)(c0 + c) * ldc, Cb[r + c * ldb]);
   }
   if (TS)
     for (int idx = tid; idx < nref * cw; idx += NTHREADS) {

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <cmath>
 #include <atomic>
 #include <cstdint>
 #include <cstdlib>
@@ -39,6 +41,12 @@ std::atomic<int64_t> g_trace_cap{0};
 int g_ctas_per_sm = 0;
 int g_split = 0;
 int g_order = 1;  // ticket order of the flat tree: 0 earliest start time, 1 list schedule
+int g_wpanel = 150;  // list-schedule cost of GEQRT/TSQRT, percent of their flops
+int g_wunmqr = 100;  // list-schedule cost of UNMQR, percent of its flops
+// measured task costs (GEQRT, UNMQR, TSQRT, TSMQR service times, any unit)
+// per (precision, NB, IB), installed by qr_set_task_costs; they replace the
+// flop-count weights of the list schedule for that configuration
+std::map<std::tuple<int, int, int>, std::array<double, 4>> g_costs;
 int g_grid_limit = 0;
 int64_t g_drop_task = -1;
 int g_record = 0;
@@ -98,8 +106,9 @@ Layout make_layout(int64_t m, int64_t n, int nb, int ib, size_t esz) {
 // earlier, so the result is a topological order.
 struct SchedKey {
   int MT, NT, S, order;
+  double wG, wU, wT, wM;
   bool operator<(const SchedKey& o) const {
-    return std::tie(MT, NT, S, order) < std::tie(o.MT, o.NT, o.S, o.order);
+    return std::tie(MT, NT, S, order, wG, wU, wT, wM) < std::tie(o.MT, o.NT, o.S, o.order, o.wG, o.wU, o.wT, o.wM);
   }
 };
 struct Sched {
@@ -108,8 +117,20 @@ struct Sched {
 };
 std::map<SchedKey, Sched> g_sched;
 
-const Sched& get_schedule(int MT, int NT, int S) {
-  SchedKey key{MT, NT, S, g_order};
+// List-schedule weights of the four task types for a configuration: the
+// measured costs when installed, else flop counts (units of NB^3) with the
+// panel tasks weighted up by QR_OPT_PANEL_WEIGHT and UNMQR by
+// QR_OPT_UNMQR_WEIGHT (their level-2 and triangular parts run below the
+// update's rate).
+std::array<double, 4> task_weights(int prec, int nb, int ib, int S) {
+  auto it = g_costs.find(std::make_tuple(prec, nb, ib));
+  if (it != g_costs.end()) return it->second;
+  const double ap = g_wpanel / 100.0, au = g_wunmqr / 100.0;
+  return {4.0 / 3.0 * ap, 2.0 * au / S, 2.0 * ap, 4.0 / S};
+}
+
+const Sched& get_schedule(int MT, int NT, int S, const std::array<double, 4>& w) {
+  SchedKey key{MT, NT, S, g_order, w[0], w[1], w[2], w[3]};
   auto it = g_sched.find(key);
   if (it != g_sched.end()) return it->second;
   const int K = std::min(MT, NT);
@@ -137,9 +158,7 @@ const Sched& get_schedule(int MT, int NT, int S) {
     wt.push_back(w);
     cur.clear();
   };
-  // relative costs (units of NB^3 flops); panel tasks run a latency-bound
-  // level-2 part, so they are weighted up a little
-  const double wG = 4.0 / 3.0 * 1.5, wT = 2.0 * 1.5, wU = 2.0 / S, wM = 4.0 / S;
+  const double wG = w[0], wU = w[1], wT = w[2], wM = w[3];
   for (int k = 0; k < K; ++k) {
     {
       double st = 0;
@@ -375,7 +394,7 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
   const Layout L = make_layout(m, n, nb, ib, sizeof(S));
   if (scratch_bytes < (int64_t)L.bytes) return -9;
   if (L.MT > 65535 || L.NT > 65535) return -1;
-  const Sched& sc = get_schedule(L.MT, L.NT, L.S);
+  const Sched& sc = get_schedule(L.MT, L.NT, L.S, task_weights(sizeof(S) == 8 ? QR_PREC_F64 : QR_PREC_F32, nb, ib, L.S));
   char* base = (char*)scratch;
   DevCtl* ctl = (DevCtl*)base;
   unsigned* cnt = (unsigned*)(base + L.off_cnt);
@@ -520,16 +539,21 @@ int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, in
 
 }  // namespace
 
-int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib) {
+int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib, int prec) {
   if (m < 1 || n < 1 || n > m || nb < 8 || nb > 512) return -1;
   std::lock_guard<std::mutex> lock(g_mu);
   const Layout L = make_layout(m, n, nb, ib, 8);
   if (L.MT > 65535 || L.NT > 65535) return -1;
-  get_schedule(L.MT, L.NT, L.S);
+  get_schedule(L.MT, L.NT, L.S, task_weights(prec, nb, ib, L.S));
   return 0;
 }
 
 // ---------------------------------------------------------------------------
+std::array<double, 4> qr_task_weights(int prec, int nb, int ib, int S) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return task_weights(prec, nb, ib, S);
+}
+
 void qr_trace_target(void** buf, int64_t* cap) {
   *buf = g_trace.load();
   *cap = g_trace_cap.load();
@@ -587,6 +611,21 @@ int qr_status(const void* scratch, int* status, void* stream) {
   return 0;
 }
 
+int qr_set_task_costs(int prec, int nb, int ib, const double* costs) {
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -1;
+  if (nb < 8 || nb > 512) return -2;
+  if (ib < 1 || ib > nb || ib > 256) return -3;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!costs) {
+    g_costs.erase(std::make_tuple(prec, nb, ib));
+    return 0;
+  }
+  for (int q = 0; q < 4; ++q)
+    if (!(costs[q] > 0.0) || !std::isfinite(costs[q])) return -4;
+  g_costs[std::make_tuple(prec, nb, ib)] = {costs[0], costs[1], costs[2], costs[3]};
+  return 0;
+}
+
 int qr_set_trace(void* d_buf, int64_t capacity) {
   if (capacity < 0) return -2;
   if (d_buf && ((uintptr_t)d_buf & 31)) return -1;
@@ -633,6 +672,14 @@ int qr_set_option(int opt, int64_t value) {
       if (value != 0 && value != 1) return -2;
       g_order = (int)value;
       return 0;
+    case QR_OPT_PANEL_WEIGHT:
+      if (value < 10 || value > 10000) return -2;
+      g_wpanel = (int)value;
+      return 0;
+    case QR_OPT_UNMQR_WEIGHT:
+      if (value < 10 || value > 10000) return -2;
+      g_wunmqr = (int)value;
+      return 0;
   }
   return -1;
 }
@@ -647,6 +694,8 @@ int64_t qr_get_option(int opt) {
     case QR_OPT_DROP_TASK: return g_drop_task;
     case QR_OPT_RECORD_EVENTS: return g_record;
     case QR_OPT_ORDER: return g_order;
+    case QR_OPT_PANEL_WEIGHT: return g_wpanel;
+    case QR_OPT_UNMQR_WEIGHT: return g_wunmqr;
   }
   return INT64_MIN;
 }

@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <array>
 #include <cstdint>
 
 #include "../../include/tileqr.h"
@@ -30,8 +31,14 @@ int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib, int*
 
 // Builds (and caches) the host task order for this shape so that a later
 // timed qr_factor_* call does not include it. Returns 0 on success.
-int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib);
+int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib, int prec);
 
 // The trace buffer set by qr_set_trace (null when tracing is off) and its
 // capacity in records; read at each launch of a persistent kernel.
 void qr_trace_target(void** buf, int64_t* cap);
+
+// List-schedule weights (GEQRT, UNMQR, TSQRT, TSMQR) for factorizations at
+// precision prec with (nb, ib) and S column chunks: the measured costs set by
+// qr_set_task_costs, else flop counts with the panel and UNMQR factors of
+// QR_OPT_PANEL_WEIGHT / QR_OPT_UNMQR_WEIGHT.
+std::array<double, 4> qr_task_weights(int prec, int nb, int ib, int S);

@@ -97,15 +97,19 @@ int sched_workers() {
 
 struct DagKey {
   int MT, NT, S, P, last_short;
+  double w0, w1, w2, w3;  // list-schedule weights (factorization DAGs)
   bool operator<(const DagKey& o) const {
-    return std::tie(MT, NT, S, P, last_short) < std::tie(o.MT, o.NT, o.S, o.P, o.last_short);
+    return std::tie(MT, NT, S, P, last_short, w0, w1, w2, w3) <
+           std::tie(o.MT, o.NT, o.S, o.P, o.last_short, o.w0, o.w1, o.w2, o.w3);
   }
 };
 std::map<DagKey, Dag> g_dags;
 
 // Factorization DAG.
-const Dag& factor_dag(int MT, int NT, int S, int P, bool last_short) {
-  DagKey key{MT, NT, S, P, last_short ? 1 : 0};
+// w: list-schedule costs of GEQRT, UNMQR, TSQRT, TSMQR (qr_task_weights);
+// the triangle-on-triangle tasks count half of their TS counterparts.
+const Dag& factor_dag(int MT, int NT, int S, int P, bool last_short, const std::array<double, 4>& w) {
+  DagKey key{MT, NT, S, P, last_short ? 1 : 0, w[0], w[1], w[2], w[3]};
   auto it = g_dags.find(key);
   if (it != g_dags.end()) return it->second;
   const int K = std::min(MT, NT);
@@ -143,9 +147,7 @@ const Dag& factor_dag(int MT, int NT, int S, int P, bool last_short) {
     t.k = k;
     return t;
   };
-  // relative task durations (units of NB^3 flops on one CTA); panels carry
-  // latency-bound level-2 work and are weighted up
-  const double wG = 2.0, wT = 3.0, wTT = 1.5, wU = 2.0 / S, wM = 4.0 / S, wMT = 2.0 / S;
+  const double wG = w[0], wU = w[1], wT = w[2], wM = w[3], wTT = 0.5 * w[2], wMT = 0.5 * w[3];
   auto panel1 = [&](int type, int h, int k, double w) {  // GEQRT on (h,k)
     TaskRec t = rec(type, 0, h, h, k, k);
     t.ctop = W(h, k, 0);
@@ -247,7 +249,7 @@ const Dag& factor_dag(int MT, int NT, int S, int P, bool last_short) {
 // Q application DAG over C's row blocks (column chunks S). Program order is
 // the factorization's update order for Q^T, reversed for Q.
 const Dag& apply_dag(int MT, int NT, int S, int P, bool last_short, int tr) {
-  DagKey key{MT, NT, S, -P - 1 - 1000 * tr, last_short ? 1 : 0};
+  DagKey key{MT, NT, S, -P - 1 - 1000 * tr, last_short ? 1 : 0, 0.0, 0.0, 0.0, 0.0};
   auto it = g_dags.find(key);
   if (it != g_dags.end()) return it->second;
   const int K = std::min(MT, NT);
@@ -342,7 +344,10 @@ PLayout p_layout(int64_t m, int64_t n, int nb, int ib, int p, size_t esz, bool w
   L.P = std::max(1, p);
   const int64_t last_rows = m - (int64_t)(L.MT - 1) * nb;
   L.last_short = last_rows < std::min<int64_t>(nb, n);
-  L.ntasks = with_tasks ? (int64_t)factor_dag(L.MT, L.NT, L.S, L.P, L.last_short).tasks.size() : 0;
+  L.ntasks = with_tasks ? (int64_t)factor_dag(L.MT, L.NT, L.S, L.P, L.last_short,
+                                               qr_task_weights(esz == 8 ? QR_PREC_F64 : QR_PREC_F32, nb, ib, L.S))
+                                     .tasks.size()
+                        : 0;
   size_t off = 256;
   L.off_cnt = off;
   off = al256(off + (size_t)L.MT * L.NT * L.S * 4);
@@ -491,7 +496,8 @@ int factor_p_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, int p
   if ((m + nb - 1) / nb > 65535) return -1;
   const PLayout L = p_layout(m, n, nb, ib, p, sizeof(S), true);
   if (scratch_bytes < (int64_t)L.bytes) return -10;
-  const Dag& dag = factor_dag(L.MT, L.NT, L.S, L.P, L.last_short);
+  const Dag& dag = factor_dag(L.MT, L.NT, L.S, L.P, L.last_short,
+                             qr_task_weights(sizeof(S) == 8 ? QR_PREC_F64 : QR_PREC_F32, nb, ib, L.S));
   char* base = (char*)scratch;
   cudaError_t e = cudaMemcpyAsync(base + L.off_tasks, dag.tasks.data(), dag.tasks.size() * sizeof(TaskRec),
                                   cudaMemcpyHostToDevice, st);

@@ -286,7 +286,7 @@ int time_factor(int64_t m, int64_t n, int nb, int ib, int pd, int reps, void* wo
   cudaEventCreate(&e1);
   // the task order is built (and cached) on the host outside the timed runs;
   // small problems also get one untimed warm-up run
-  qr_prepare_schedule(m, n, nb, ib);
+  qr_prepare_schedule(m, n, nb, ib, sizeof(S) == 8 ? QR_PREC_F64 : QR_PREC_F32);
   const int warm = (m * n <= 4000000) ? 1 : 0;
   for (int r = 1 - warm; r < reps + 1; ++r) {
     fill_uniform<S><<<1184, 256, 0, st>>>(A, m * n, (uint64_t)(m * 31 + n), -0.5, 0.5);

@@ -122,3 +122,23 @@ def test_every_declared_symbol_is_exported(L):
         assert hasattr(L, nm), nm
     declared = {s[0] for s in lib_mod.SIGNATURES}
     assert names == declared, (names ^ declared)
+
+
+def test_task_costs_and_schedule_options_validate(L):
+    """Host-only settings of the list schedule: measured task costs and the
+    flop-weight options reject bad arguments and accept good ones."""
+    good = _da([2.5, 1.8, 2.7, 2.2])
+    assert L.qr_set_task_costs(0, 128, 8, good) == 0
+    assert L.qr_set_task_costs(0, 128, 8, None) == 0  # removed again
+    assert L.qr_set_task_costs(2, 128, 8, good) == -1
+    assert L.qr_set_task_costs(0, 4, 2, good) == -2
+    assert L.qr_set_task_costs(0, 128, 0, good) == -3
+    assert L.qr_set_task_costs(1, 64, 16, _da([1.0, -1.0, 1.0, 1.0])) == -4
+    assert L.qr_set_task_costs(1, 64, 16, _da([1.0, float("nan"), 1.0, 1.0])) == -4
+    for opt, default in ((8, 150), (9, 100)):
+        assert L.qr_get_option(opt) == default
+        assert L.qr_set_option(opt, 5) == -2
+        assert L.qr_set_option(opt, 300) == 0 and L.qr_get_option(opt) == 300
+        assert L.qr_set_option(opt, default) == 0
+    assert L.qr_set_trace(None, 0) == 0
+    assert L.qr_set_trace(None, -1) == -2
