@@ -15,6 +15,10 @@ that the package installs at first use.
     python -m paper_1102_5328_gb300.calibrate --table paper_1102_5328_gb300/tuned/gb300_fp64.json \
         --out paper_1102_5328_gb300/tuned/gb300_fp64_costs.json
 
+`--report N,NB,IB` prints per-type service and wait times and the busy
+fraction of the persistent CTAs over the run of one traced factorization
+(`--flop-weights` first removes the measured costs of that pair).
+
 Orchestration only: every traced run is qr_factor_d/_s.
 """
 import argparse
@@ -30,10 +34,9 @@ from . import lib, qr_factor, qr_set_task_costs, qr_set_trace, read_trace
 TYPES = ("GEQRT", "UNMQR", "TSQRT", "TSMQR")
 
 
-def measure(n, nb, ib, dtype, seed=7):
-    """Median service time (us) per task type of one traced flat-tree
-    factorization of an n x n uniform[-0.5, 0.5) matrix, and the run's
-    wall time (ms) from the trace."""
+def trace_run(n, nb, ib, dtype, seed=7):
+    """One traced flat-tree factorization of an n x n uniform[-0.5, 0.5)
+    matrix (after an untraced warm-up): read_trace's arrays."""
     g = torch.Generator(device="cuda").manual_seed(seed)
     A0 = (torch.rand(n, n, device="cuda", generator=g, dtype=dtype) - 0.5).t()
     ntasks = lib().qr_task_count(n, n, nb, ib)
@@ -48,10 +51,38 @@ def measure(n, nb, ib, dtype, seed=7):
         torch.cuda.synchronize()
     finally:
         qr_set_trace(None)
-    _, typ, _, _, t_ready, t_done = read_trace(buf, ntasks)
+    return read_trace(buf, ntasks)
+
+
+def measure(n, nb, ib, dtype, seed=7):
+    """Median service time (us) per task type of one traced factorization,
+    the task counts, and the run's span (ms) from the trace."""
+    _, typ, _, _, t_ready, t_done = trace_run(n, nb, ib, dtype, seed)
     svc = (t_done - t_ready) / 1e3
     costs = [float(np.median(svc[typ == t])) for t in range(4)]
     return costs, [int((typ == t).sum()) for t in range(4)], float(t_done.max()) / 1e6
+
+
+def report(n, nb, ib, dtype, workers, bins=10):
+    """Per task type: count, median/p90 service and wait (us), share of the
+    workers' time; and the fraction of worker slots busy in each tenth of
+    the run."""
+    _, typ, _, t_take, t_ready, t_done = trace_run(n, nb, ib, dtype)
+    span = float(t_done.max())
+    rows = []
+    for t in range(4):
+        sel = typ == t
+        svc = (t_done - t_ready)[sel] / 1e3
+        wt = (t_ready - t_take)[sel] / 1e3
+        rows.append({"type": TYPES[t], "count": int(sel.sum()), "service_med_us": float(np.median(svc)),
+                     "service_p90_us": float(np.percentile(svc, 90)), "wait_med_us": float(np.median(wt)),
+                     "share": float(svc.sum() * 1e3 / (span * workers))})
+    edges = np.linspace(0.0, span, bins + 1)
+    busy = np.zeros(bins)
+    for k in range(bins):
+        lo, hi = edges[k], edges[k + 1]
+        busy[k] = np.clip(np.minimum(t_done, hi) - np.maximum(t_ready, lo), 0, None).sum() / (workers * (hi - lo))
+    return {"n": n, "nb": nb, "ib": ib, "span_ms": span / 1e6, "types": rows, "busy_per_tenth": busy.round(3).tolist()}
 
 
 def calibrate(table, passes=2, n_cap=10000):
@@ -79,12 +110,26 @@ def calibrate(table, passes=2, n_cap=10000):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--table", required=True)
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--table", help="tuning table whose flat-tree pairs are calibrated")
+    ap.add_argument("--out", help="cost file to write")
     ap.add_argument("--passes", type=int, default=2)
     ap.add_argument("--n-cap", type=int, default=10000)
+    ap.add_argument("--report", default="", help="N,NB,IB: print a trace report of one factorization instead")
+    ap.add_argument("--prec", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--flop-weights", action="store_true", help="report: clear measured costs first")
     a = ap.parse_args(argv)
     torch.cuda.set_device(0)
+    if a.report:
+        n, nb, ib = (int(v) for v in a.report.split(","))
+        dtype = torch.float32 if a.prec == "f32" else torch.float64
+        lib()
+        if a.flop_weights:
+            qr_set_task_costs(dtype, nb, ib, None)
+        workers = 2 * torch.cuda.get_device_properties(0).multi_processor_count
+        print(json.dumps(report(n, nb, ib, dtype, workers), indent=1))
+        return 0
+    if not a.table or not a.out:
+        ap.error("--table and --out are required unless --report is given")
     res = calibrate(a.table, a.passes, a.n_cap)
     s = json.dumps(res, indent=1)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)

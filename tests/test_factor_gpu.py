@@ -219,3 +219,25 @@ def test_task_trace(q):
     assert np.all(t_take <= t_ready) and np.all(t_ready <= t_done)
     assert sm.max() < torch.cuda.get_device_properties(0).multi_processor_count
     assert np.all(buf[ntasks:].cpu().numpy() == -1)
+
+
+def test_ticket_order_weights_are_bitwise_neutral(q):
+    """Measured task costs and the flop-weight options only reorder the
+    tickets: the factorization is bitwise the same under every order."""
+    A = inputs.uniform_matrix(900, 700, seed=6)
+    q.qr_set_task_costs(torch.float64, 64, 8, None)
+    f1 = _gpu_factor(q, A, 64, 8)
+    q.qr_set_task_costs(torch.float64, 64, 8, [9.0, 1.0, 7.0, 2.0])
+    try:
+        f2 = _gpu_factor(q, A, 64, 8)
+    finally:
+        q.qr_set_task_costs(torch.float64, 64, 8, None)
+    q.qr_set_option(q.QR_OPT_PANEL_WEIGHT, 500)
+    q.qr_set_option(q.QR_OPT_UNMQR_WEIGHT, 20)
+    try:
+        f3 = _gpu_factor(q, A, 64, 8)
+    finally:
+        q.qr_set_option(q.QR_OPT_PANEL_WEIGHT, 150)
+        q.qr_set_option(q.QR_OPT_UNMQR_WEIGHT, 100)
+    assert torch.equal(f1.A, f2.A) and torch.equal(f1.T, f2.T)
+    assert torch.equal(f1.A, f3.A) and torch.equal(f1.T, f3.T)
