@@ -39,6 +39,24 @@ SEED = 10000
 TRAFFIC_BYTES = {(10000, 10000, 128, 8): 67.71e9 + 42.61e9}
 
 
+def max_over_ranks(x, device="cuda"):
+    """The maximum of a per-rank float over all ranks (the job takes as long
+    as its slowest rank); the value itself with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(flops_per_step, steps, ranks, max_ms):
+    """GFLOP/s of the whole job: every rank factors its own matrix (replicas),
+    so the credited flops add up over ranks; the time is the slowest rank's."""
+    return flops_per_step * steps * ranks / (max_ms * 1e-3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -418,12 +436,9 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms)
     flops = q.qr_flops(m, n)
-    value = flops * args.steps * ws / (total_ms * 1e-3) / 1e9
+    value = whole_job_gflops(flops, args.steps, ws, total_ms)
     kavg = sum(kernel_ms) / len(kernel_ms)
     nominal_peak = 152 * 2 * 2 * 2.070e9 / 1e12  # TFLOP/s: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
     achieved = flops / (kavg * 1e-3) / 1e12
@@ -461,11 +476,8 @@ def main():
         eb.record(stream)
         torch.cuda.synchronize()
         ems = ea.elapsed_time(eb)
-        if ws > 1:
-            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": flops * ks * ws / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
+        ems = max_over_ranks(ems)
+        e2e = {"value": whole_job_gflops(flops, ks, ws, ems), "unit": "GFLOP/s",
                "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * t_elems,
                "steps": ks}
 
