@@ -17,7 +17,7 @@ library's C++ tuner makes. Only tests/ (and bench.py's CPU baseline) use it.
   * interpolation: an untuned request uses the closest benchmarked point
     (Sec. 5.1).
 
-Readings where the paper is silent (listed with the rest in the design doc):
+Readings where the paper is silent:
 upper hull taken left to right with both end points, collinear middle points
 dropped; steepness of a hull point = slope of the hull segment that ends at
 it, the leftmost point's segment starting at the origin; Heuristic 1 sorts
