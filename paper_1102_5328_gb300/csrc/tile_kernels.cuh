@@ -289,12 +289,21 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
               if (q < pgc) pbuf[(q * G + g) * cw + c] = acc[q];
           }
           __syncthreads();
-          for (int o = tid; o < pgc * cw; o += NTHREADS) {
+          // two outputs per thread per pass, both top-row loads issued
+          // before either sum (one L2 round trip instead of two)
+          for (int o = tid; o < pgc * cw; o += 2 * NTHREADS) {
+            const int o2 = o + NTHREADS;
+            const bool two = o2 < pgc * cw;
             const int q = o / cw, cc = o - (o / cw) * cw;
-            const int p = pp0 + pg0 + q;
-            S s = TS ? ldg(Ctop + (l0 + p) + (size_t)(cs + cc) * ldct) : S(0);
+            const int q2 = two ? o2 / cw : q, cc2 = two ? o2 - (o2 / cw) * cw : cc;
+            S s = TS ? ldg(Ctop + (l0 + pp0 + pg0 + q) + (size_t)(cs + cc) * ldct) : S(0);
+            S s2 = (TS && two) ? ldg(Ctop + (l0 + pp0 + pg0 + q2) + (size_t)(cs + cc2) * ldct) : S(0);
             for (int gg = glo; gg < ghi; ++gg) s += pbuf[(q * G + gg) * cw + cc];
-            sm.w[p * cw + cc] = s;
+            sm.w[(pp0 + pg0 + q) * cw + cc] = s;
+            if (two) {
+              for (int gg = glo; gg < ghi; ++gg) s2 += pbuf[(q2 * G + gg) * cw + cc2];
+              sm.w[(pp0 + pg0 + q2) * cw + cc2] = s2;
+            }
           }
           __syncthreads();
         }
@@ -307,12 +316,15 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         // ib * cw <= W_CAP = 16 * NTHREADS: at most 16 outputs per thread,
         // held in registers (compile-time indices) until every read of W is done
         S wq[16];
+        S cold[4];  // TS: the first four outputs' top rows, loaded before the barrier
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int o = tid + u * NTHREADS;
           S s = S(0);
+          if (u < 4) cold[u] = S(0);
           if (o < ib * cw) {
             const int p = o / cw, cc = o - (o / cw) * cw;
+            if (TS && u < 4) cold[u] = ldg(Ctop + (l0 + p) + (size_t)(cs + cc) * ldct);
             if (TR) {
               const S* tcol = Tb + (size_t)p * ldtb;
               for (int q = 0; q <= p; ++q) s = fma(ldx(tcol + q, tsm), sm.w[q * cw + cc], s);
@@ -332,7 +344,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
             sm.w[p * cw + cc] = wq[u];
             if (TS) {
               S* pt = Ctop + (l0 + p) + (size_t)(cs + cc) * ldct;
-              stg(pt, ldg(pt) - wq[u]);
+              stg(pt, (u < 4 ? cold[u < 4 ? u : 0] : ldg(pt)) - wq[u]);
             }
           }
         }
