@@ -145,10 +145,27 @@ __device__ __forceinline__ S cta_sum(S v, S* red) {
 // TS tri: zero below it); zero past `rows`. GE: four loads in flight per
 // thread. TS: one (its later blocks come through the cp.async prefetch of
 // apply_qt, and the TS update keeps more registers live).
+// TS with use_async (no triangle mask, V and ldv 16-byte aligned): 16-byte
+// cp.async copies, zero-filled past `rows`, all in flight at once; the
+// caller issues cp.async.wait_all before the barrier that publishes them.
 template <typename S, bool TS>
 __device__ __forceinline__ void stage_refl(S* buf, const S* V, int ldv, int nr, int r0, int rows, int pc0, int pb,
-                                           bool tri) {
+                                           bool tri, bool use_async = false) {
   if constexpr (TS) {
+    if (use_async) {
+      constexpr int EPC = 16 / sizeof(S);
+      const int half = nr / EPC;  // nr is a multiple of 32, so of EPC
+      for (int idx = threadIdx.x; idx < pb * half; idx += NTHREADS) {
+        const int p = idx / half, rl = EPC * (idx - (idx / half) * half), r = rl + r0;
+        const int valid = r < rows ? min(EPC, rows - r) * (int)sizeof(S) : 0;
+        const S* src = V + (valid ? r + (size_t)(pc0 + p) * ldv : 0);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + p * nr + rl);
+        const size_t gsrc = __cvta_generic_to_global(src);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gsrc), "r"(valid) : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      return;  // the caller waits (cp.async.wait_all) before its barrier
+    }
     for (int idx = threadIdx.x; idx < pb * nr; idx += NTHREADS) {
       const int p = idx / nr, rl = idx - (idx / nr) * nr;
       const int r = rl + r0, pc = pc0 + p;
@@ -217,6 +234,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       const int r = g * RPT + rr;
       creg[rr] = (act && r < rows) ? ldg(C + r + (size_t)(cs + c) * ldc) : S(0);
     }
+    int tsel = 0;           // which half of ts holds the current block's T (t_in_ts)
     int vcur = 0;           // which buffer holds the current block's V (0: vs, 1: part)
     bool staged = false;    // current block's V (and T in ts) already in place
     for (int bi = 0; bi < nblk; ++bi) {
@@ -237,19 +255,21 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       if (PB > ib) PB = ib;
       if (PB < 1) PB = 1;
       const bool myrows = act && g >= glo && g < ghi;
-      // T_l in shared memory (ts) unless it is there already
+      // T_l in shared memory: half tsel of ts (tsel = 1 only after a T
+      // prefetch, which needs ib * ib <= NTHREADS, so the block fits there)
       const bool t_in_ts = !t_smem && ib * ib <= TS_CAP;
       // --- phase A: W = Vfull^T Cstack, V staged PB reflectors at a time
       for (int pp0 = 0; pp0 < ib; pp0 += PB) {
         const int pb = min(PB, ib - pp0);
         if (!staged) {
           __syncthreads();
-          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri);
+          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri, can_pipe);
           if (pp0 == 0 && t_in_ts)
             for (int idx = tid; idx < ib * ib; idx += NTHREADS) {
               const int p = idx / ib, q = idx - (idx / ib) * ib;
-              sm.ts[idx] = (q <= p) ? ldg(T + q + (size_t)(l0 + p) * ldt) : S(0);
+              sm.ts[tsel * (TS_CAP / 2) + idx] = (q <= p) ? ldg(T + q + (size_t)(l0 + p) * ldt) : S(0);
             }
+          asm volatile("cp.async.wait_all;" ::: "memory");
           __syncthreads();
         }
         for (int pg0 = 0; pg0 < pb; pg0 += PG) {
@@ -310,7 +330,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       }
       // --- phase B: W <- T_l^T W (Q^T) or T_l W (Q); TS: Ctop rows -= W
       {
-        const S* Tb = t_in_ts ? sm.ts : T + (size_t)l0 * ldt;  // (q, p) at Tb[q + p * ldtb]
+        const S* Tb = t_in_ts ? sm.ts + tsel * (TS_CAP / 2) : T + (size_t)l0 * ldt;  // (q, p) at Tb[q + p * ldtb]
         const int ldtb = t_in_ts ? ib : ldt;
         const bool tsm = t_in_ts || t_smem;
         // ib * cw <= W_CAP = 16 * NTHREADS: at most 16 outputs per thread,
@@ -382,7 +402,8 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         const int pb = min(PB, ib - pp0);
         if (PB < ib) {
           __syncthreads();
-          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri);
+          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri, can_pipe);
+          asm volatile("cp.async.wait_all;" ::: "memory");
           __syncthreads();
         }
         if (myrows) {
@@ -407,9 +428,11 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         }
       }
       if (pre) {
+        // the next T goes to the other half of ts (phase C reads neither),
+        // so one barrier publishes it together with the copied reflectors
         asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();  // every thread's phase C reads of ts/vbuf are done
-        if (!t_smem && tid < ibn * ibn) sm.ts[tid] = tpre;
+        if (!t_smem && tid < ibn * ibn) sm.ts[(tsel ^ 1) * (TS_CAP / 2) + tid] = tpre;
+        tsel ^= 1;
         vcur ^= 1;
         staged = true;
         __syncthreads();
