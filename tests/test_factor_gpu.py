@@ -241,3 +241,18 @@ def test_ticket_order_weights_are_bitwise_neutral(q):
         q.qr_set_option(q.QR_OPT_UNMQR_WEIGHT, 100)
     assert torch.equal(f1.A, f2.A) and torch.equal(f1.T, f2.T)
     assert torch.equal(f1.A, f3.A) and torch.equal(f1.T, f3.T)
+
+
+def test_calibration_measures_every_task_type(q):
+    """calibrate.measure on a small order: one positive median service time
+    per task type, task counts matching the flat tree's DAG, and a report
+    whose busy fractions lie in [0, 1]."""
+    from paper_1102_5328_gb300 import calibrate
+    n, nb, ib = 640, 64, 16
+    costs, counts, span_ms = calibrate.measure(n, nb, ib, torch.float64)
+    nt = n // nb
+    assert counts == [nt, nt * (nt - 1) // 2, nt * (nt - 1) // 2, sum(k * k for k in range(nt))]
+    assert all(c > 0 for c in costs) and span_ms > 0
+    rep = calibrate.report(n, nb, ib, torch.float64, 2 * torch.cuda.get_device_properties(0).multi_processor_count)
+    assert all(0.0 <= b <= 1.0 + 1e-9 for b in rep["busy_per_tenth"])
+    assert [t["count"] for t in rep["types"]] == counts
