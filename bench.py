@@ -328,18 +328,25 @@ def run_step1(args):
     torch.cuda.set_device(0)
     L = q.lib()
     nb, ib = args.nb or 128, args.ib or 8
+    prec = 1 if args.prec == "f32" else 0
     b = ctypes.c_int64()
-    q._lib.check(L.qr_step1_workspace(nb, 0, ctypes.byref(b)), "qr_step1_workspace")
+    q._lib.check(L.qr_step1_workspace(nb, prec, ctypes.byref(b)), "qr_step1_workspace")
     work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
     s, g = ctypes.c_double(), ctypes.c_double()
     for _ in range(max(1, args.warmup)):
-        q._lib.check(L.qr_step1_time(nb, ib, 0, 3, ctypes.byref(s), ctypes.byref(g), ctypes.c_void_p(work.data_ptr()),
+        q._lib.check(L.qr_step1_time(nb, ib, prec, 3, ctypes.byref(s), ctypes.byref(g), ctypes.c_void_p(work.data_ptr()),
                                      b.value, q._stream_ptr()), "qr_step1_time")
-    q._lib.check(L.qr_step1_time(nb, ib, 0, max(args.steps, 3), ctypes.byref(s), ctypes.byref(g),
+    q._lib.check(L.qr_step1_time(nb, ib, prec, max(args.steps, 3), ctypes.byref(s), ctypes.byref(g),
                                  ctypes.c_void_p(work.data_ptr()), b.value, q._stream_ptr()), "qr_step1_time")
     peak = q.qr_peak_fp64()
-    print(json.dumps({"workload": "Step-1 TSMQR batch, NB=%d IB=%d" % (nb, ib), "ms_per_launch": s.value * 1e3,
-                      "gflops": g.value, "fp64_peak_live_gflops": peak, "frac_of_live_peak": g.value / peak}))
+    line = {"workload": "Step-1 TSMQR batch, %s, NB=%d IB=%d" % (args.prec, nb, ib), "ms_per_launch": s.value * 1e3,
+            "gflops": g.value}
+    if prec == 0:
+        line.update({"fp64_peak_live_gflops": peak, "frac_of_live_peak": g.value / peak})
+    else:
+        fp32_peak = 152 * 128 * 2 * 2.070  # GFLOP/s: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
+        line.update({"fp32_peak_derived_gflops": fp32_peak, "frac_of_fp32_peak": g.value / fp32_peak})
+    print(json.dumps(line))
     return 0
 
 
@@ -354,6 +361,7 @@ def main():
     ap.add_argument("--ib", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"], help="step1: precision of the TSMQR batch")
     ap.add_argument("--workload", default="qr", choices=["qr", "batched", "ls", "step1"],
                     help="qr: the headline line; batched / ls: the extension workloads (own JSON lines)")
     ap.add_argument("--count", type=int, default=4096)
