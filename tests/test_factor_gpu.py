@@ -256,3 +256,29 @@ def test_calibration_measures_every_task_type(q):
     rep = calibrate.report(n, nb, ib, torch.float64, 2 * torch.cuda.get_device_properties(0).multi_processor_count)
     assert all(0.0 <= b <= 1.0 + 1e-9 for b in rep["busy_per_tenth"])
     assert [t["count"] for t in rep["types"]] == counts
+
+
+@pytest.mark.parametrize("m,n,nb,ib", [(777, 600, 96, 24), (1024, 1024, 128, 16), (333, 300, 64, 16)])
+def test_factor_fp32_flat_tree_budget(q, m, n, nb, ib):
+    """FP32 flat-tree factorization (the FP32 update path with 16-byte shared
+    loads): R agrees with the oracle's QR of the FP32-rounded input, up to
+    row signs, within 10 n u_32, and Q^T A reproduces R to the same budget."""
+    A = inputs.uniform_matrix(m, n, seed=m + 3 * n)
+    A32 = A.astype(np.float32).astype(np.float64)
+    def dev32(x):
+        return torch.from_numpy(np.ascontiguousarray(x.T).astype(np.float32)).cuda().t()
+
+    f = q.qr_factor(dev32(A), nb, ib, p=1)
+    torch.cuda.synchronize()
+    R = np.triu(f.A[:n].double().cpu().numpy())
+    F, _ = oracle.geqr2(A32)
+    R_or = np.triu(F[:n])
+    D = oracle.row_signs(R, R_or)
+    u32 = 2.0 ** -24
+    assert np.linalg.norm(D[:, None] * R - R_or) / np.linalg.norm(R_or) <= 10 * n * u32
+    C = dev32(A)
+    q.qr_apply_qt(f, C, trans=True)
+    QtA = C.double().cpu().numpy()
+    assert np.linalg.norm(np.triu(QtA[:n]) - R) / np.linalg.norm(R) <= 10 * n * u32
+    if m > n:
+        assert np.linalg.norm(QtA[n:]) / np.linalg.norm(R) <= 10 * n * u32
