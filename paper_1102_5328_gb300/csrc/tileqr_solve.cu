@@ -121,10 +121,15 @@ __global__ void __launch_bounds__(TB) trsm_wave(int n, const S* __restrict__ R, 
     if (wid < nk) {
       const int k = wid;
       S y0 = ys[lane * 8 + k], y1 = ys[(lane + 32) * 8 + k];
+      // reciprocals of the diagonal, formed off the substitution chain; the
+      // chain itself is then one shuffle, one multiply and one FMA per row
+      const S ri0 = lane < nr ? S(1) / Rb[lane * TRSM_LD + lane] : S(0);
+      const S ri1 = lane + 32 < nr ? S(1) / Rb[(lane + 32) * TRSM_LD + lane + 32] : S(0);
       for (int t = 0; t < nr; ++t) {
         const int j = trans ? t : nr - 1 - t;
         const S v = __shfl_sync(0xffffffffu, j < 32 ? y0 : y1, j & 31);
-        const S xj = v / Rb[j * TRSM_LD + j];
+        const S rj = __shfl_sync(0xffffffffu, j < 32 ? ri0 : ri1, j & 31);
+        const S xj = v * rj;
         const S a0 = Rb[j * TRSM_LD + lane], a1 = Rb[j * TRSM_LD + lane + 32];
         if (trans) {
           if (lane > j) y0 = fma(-a0, xj, y0);
