@@ -1,7 +1,7 @@
 // Least squares through the tile QR: qr_solve_ls.
 //
-// FP64 path: factor a copy of A in FP64 (qr_factor_d), Y = Q^T B, X = R^{-1}
-// Y(0:n). Mixed path: factor an FP32 copy of A (FP64 only in the panel's
+// FP64 path: factor a copy of A in FP64 (qr_factor_p_d, p panel domains),
+// Y = Q^T B, X = R^{-1} Y(0:n). Mixed path: factor an FP32 copy of A (FP64 only in the panel's
 // Householder vector / tau generation), then refine on the augmented system
 // [I A; A^T 0][r; x] = [b; 0] with FP64 residuals and FP64 accumulation of x
 // and r; each correction is solved through the FP32 factors:
