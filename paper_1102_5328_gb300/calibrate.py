@@ -77,12 +77,21 @@ def report(n, nb, ib, dtype, workers, bins=10):
         rows.append({"type": TYPES[t], "count": int(sel.sum()), "service_med_us": float(np.median(svc)),
                      "service_p90_us": float(np.percentile(svc, 90)), "wait_med_us": float(np.median(wt)),
                      "share": float(svc.sum() * 1e3 / (span * workers))})
-    edges = np.linspace(0.0, span, bins + 1)
+    busy = busy_fractions(t_ready, t_done, workers, bins)
+    return {"n": n, "nb": nb, "ib": ib, "span_ms": span / 1e6, "types": rows, "busy_per_tenth": busy.round(3).tolist()}
+
+
+def busy_fractions(t_start, t_end, workers, bins=10):
+    """Fraction of `workers` slots busy in each of `bins` equal parts of
+    [0, max(t_end)], given each task's busy interval [t_start, t_end)."""
+    t_start = np.asarray(t_start, dtype=np.float64)
+    t_end = np.asarray(t_end, dtype=np.float64)
+    edges = np.linspace(0.0, float(t_end.max()), bins + 1)
     busy = np.zeros(bins)
     for k in range(bins):
         lo, hi = edges[k], edges[k + 1]
-        busy[k] = np.clip(np.minimum(t_done, hi) - np.maximum(t_ready, lo), 0, None).sum() / (workers * (hi - lo))
-    return {"n": n, "nb": nb, "ib": ib, "span_ms": span / 1e6, "types": rows, "busy_per_tenth": busy.round(3).tolist()}
+        busy[k] = np.clip(np.minimum(t_end, hi) - np.maximum(t_start, lo), 0, None).sum() / (workers * (hi - lo))
+    return busy
 
 
 def calibrate(table, passes=2, n_cap=10000):

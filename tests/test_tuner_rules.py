@@ -142,3 +142,15 @@ def test_task_costs_and_schedule_options_validate(L):
         assert L.qr_set_option(opt, default) == 0
     assert L.qr_set_trace(None, 0) == 0
     assert L.qr_set_trace(None, -1) == -2
+
+
+def test_busy_fractions_of_a_trace():
+    """The trace report's utilisation: two workers, a run of 10 time units
+    cut in 10 bins; worker A busy over [0, 10), worker B over [5, 10)."""
+    pytest.importorskip("torch")
+    from paper_1102_5328_gb300.calibrate import busy_fractions
+    b = busy_fractions([0, 5], [10, 10], workers=2, bins=10)
+    assert b.tolist() == [0.5] * 5 + [1.0] * 5
+    # tasks back to back on one worker fill it; a gap shows as idle time
+    b = busy_fractions([0, 2, 6], [2, 4, 8], workers=1, bins=4)
+    assert b.tolist() == [1.0, 1.0, 0.0, 1.0]
