@@ -36,7 +36,7 @@ SEED = 10000
 # DRAM bytes (read + write) of one persistent_qr<double> launch, from one
 # ncu capture of the same configuration and kernel sources
 # (profiles/persistent_qr_fp64_n10000.md); None for any other configuration.
-TRAFFIC_BYTES = {(10000, 10000, 128, 8): 67.08e9 + 42.06e9}
+TRAFFIC_BYTES = {(10000, 10000, 128, 8): 57.57e9 + 41.40e9}
 
 
 def max_over_ranks(x, device="cuda"):

@@ -46,7 +46,7 @@ extern "C" {
 /* Options (qr_set_option). */
 #define QR_OPT_WAIT_TIMEOUT_US 1 /* per-wait limit of the persistent scheduler (default 20 s) */
 #define QR_OPT_CTAS_PER_SM     2 /* resident CTAs per SM of the persistent kernel (0 = max) */
-#define QR_OPT_SPLIT           3 /* column chunks per update task (0 = automatic) */
+#define QR_OPT_SPLIT           3 /* column chunks per update task (0 = automatic: FP64 1 up to NB 96, 2 up to 320) */
 #define QR_OPT_GRID_LIMIT      4 /* cap on persistent CTAs (0 = all SMs); 1 = sequential */
 #define QR_OPT_DROP_TASK       5 /* test hook: omit this ticket from the task list (-1 = off) */
 #define QR_OPT_RECORD_EVENTS   6 /* 1: bracket each persistent kernel with CUDA events on its stream */
@@ -422,8 +422,10 @@ int qr_mlp_adam_step(const float *d_grads, float *d_params, float *d_m, float *d
 int qr_mlp_train(int nsamp, const float *d_X, const float *d_y, float *d_params, float *d_m, float *d_v, int steps,
                  float lr, float *d_grads, float *d_work, void *stream);
 
-/* qr_task_count -- number of tasks of the factorization DAG (diagnostics). */
-int64_t qr_task_count(int64_t m, int64_t n, int nb, int ib);
+/* qr_task_count -- number of tasks of the flat-tree factorization DAG at
+ * precision prec (QR_PREC_*; the column split of the update tasks depends on
+ * it and on QR_OPT_SPLIT). Diagnostics, and the record count of a trace. */
+int64_t qr_task_count(int64_t m, int64_t n, int nb, int ib, int prec);
 
 #ifdef __cplusplus
 }

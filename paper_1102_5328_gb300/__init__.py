@@ -354,8 +354,8 @@ def qr_peak_fp64(stream=None):
     return g.value
 
 
-def qr_task_count(m, n, nb, ib):
-    return lib().qr_task_count(m, n, nb, ib)
+def qr_task_count(m, n, nb, ib, dtype=torch.float64):
+    return lib().qr_task_count(m, n, nb, ib, _prec(dtype))
 
 
 def qr_lookup(m, n, dtype=torch.float64):

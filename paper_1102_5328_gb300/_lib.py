@@ -51,7 +51,7 @@ SIGNATURES = [
     ("qr_set_trace", c_int, [c_vp, c_i64]),
     ("qr_set_task_costs", c_int, [c_int, c_int, c_int, ctypes.POINTER(c_dbl)]),
     ("qr_get_option", c_i64, [c_int]),
-    ("qr_task_count", c_i64, [c_i64, c_i64, c_int, c_int]),
+    ("qr_task_count", c_i64, [c_i64, c_i64, c_int, c_int, c_int]),
     ("qr_last_kernel_ms", c_int, [ctypes.POINTER(ctypes.c_float)]),
     ("qr_load_table", c_int, [ctypes.c_char_p]),
     ("qr_mlp_workspace", c_int, [c_int, ctypes.POINTER(c_i64)]),

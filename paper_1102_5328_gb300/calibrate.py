@@ -29,7 +29,7 @@ import sys
 import numpy as np
 import torch
 
-from . import lib, qr_factor, qr_set_task_costs, qr_set_trace, read_trace
+from . import lib, qr_factor, qr_set_task_costs, qr_set_trace, qr_task_count, read_trace
 
 TYPES = ("GEQRT", "UNMQR", "TSQRT", "TSMQR")
 
@@ -39,7 +39,7 @@ def trace_run(n, nb, ib, dtype, seed=7):
     matrix (after an untraced warm-up): read_trace's arrays."""
     g = torch.Generator(device="cuda").manual_seed(seed)
     A0 = (torch.rand(n, n, device="cuda", generator=g, dtype=dtype) - 0.5).t()
-    ntasks = lib().qr_task_count(n, n, nb, ib)
+    ntasks = qr_task_count(n, n, nb, ib, dtype)
     buf = torch.zeros((ntasks, 4), dtype=torch.int64, device="cuda")
     A = A0.clone()
     qr_factor(A, nb, ib, p=1)  # warm-up, builds the ticket order

@@ -61,9 +61,16 @@ struct Layout {
   int64_t t_elems;
 };
 
-int auto_split(int NB) {
+// Column chunks per update task. FP64: from NB = 128 on, two chunks run as
+// separate tasks on two CTAs (measured on the GB300: N = 10000 at NB = 128
+// 1076 -> 1094 GFLOP/s, N = 8000 1028 -> 1068; the chain of panel tasks and
+// the start and end of the run get twice the parallel work, and a chunk
+// costs what the same columns cost inside one task); NB = 64 keeps one (a
+// 32-column chunk leaves three quarters of the CTA idle). FP32 tasks are
+// latency-bound and keep one chunk up to NB = 160.
+int auto_split(int NB, size_t esz) {
   if (g_split > 0) return g_split;
-  if (NB <= 160) return 1;
+  if (NB <= (esz == 8 ? 96 : 160)) return 1;
   if (NB <= 320) return 2;
   return 4;
 }
@@ -85,7 +92,7 @@ Layout make_layout(int64_t m, int64_t n, int nb, int ib, size_t esz) {
   L.m = m; L.n = n; L.NB = nb; L.IB = ib;
   L.MT = (int)((m + nb - 1) / nb);
   L.NT = (int)((n + nb - 1) / nb);
-  L.S = std::min(auto_split(nb), nb);
+  L.S = std::min(auto_split(nb, esz), nb);
   L.ntasks = count_tasks(L.MT, L.NT, L.S);
   size_t off = 256;  // status words
   L.off_cnt = off;
@@ -542,7 +549,7 @@ int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, in
 int qr_prepare_schedule(int64_t m, int64_t n, int nb, int ib, int prec) {
   if (m < 1 || n < 1 || n > m || nb < 8 || nb > 512) return -1;
   std::lock_guard<std::mutex> lock(g_mu);
-  const Layout L = make_layout(m, n, nb, ib, 8);
+  const Layout L = make_layout(m, n, nb, ib, prec == QR_PREC_F32 ? 4 : 8);
   if (L.MT > 65535 || L.NT > 65535) return -1;
   get_schedule(L.MT, L.NT, L.S, task_weights(prec, nb, ib, L.S));
   return 0;
@@ -578,10 +585,10 @@ int qr_workspace(int64_t m, int64_t n, int nb, int ib, int prec, int64_t* t_elem
   return 0;
 }
 
-int64_t qr_task_count(int64_t m, int64_t n, int nb, int ib) {
+int64_t qr_task_count(int64_t m, int64_t n, int nb, int ib, int prec) {
   if (m <= 0 || n <= 0 || nb < 8) return 0;
   std::lock_guard<std::mutex> lock(g_mu);
-  const Layout L = make_layout(m, n, nb, ib, 8);
+  const Layout L = make_layout(m, n, nb, ib, prec == QR_PREC_F32 ? 4 : 8);
   return L.ntasks;
 }
 

@@ -205,7 +205,7 @@ def test_task_trace(q):
     timestamps ordered, SM ids within the device, tracing off afterwards."""
     m, n, nb, ib = 700, 500, 64, 16
     A = torch.from_numpy(np.ascontiguousarray(inputs.uniform_matrix(m, n, seed=3).T)).cuda().t()
-    ntasks = q.lib().qr_task_count(m, n, nb, ib)
+    ntasks = q.qr_task_count(m, n, nb, ib)
     buf = torch.full((ntasks + 8, 4), -1, dtype=torch.int64, device="cuda")
     q.qr_set_trace(buf)
     try:
