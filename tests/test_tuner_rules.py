@@ -154,3 +154,27 @@ def test_busy_fractions_of_a_trace():
     # tasks back to back on one worker fill it; a gap shows as idle time
     b = busy_fractions([0, 2, 6], [2, 4, 8], workers=1, bins=4)
     assert b.tolist() == [1.0, 1.0, 0.0, 1.0]
+
+
+def test_task_count_follows_the_column_split(L):
+    """Flat-tree task counts: per panel k one GEQRT, S chunks of UNMQR per
+    trailing tile column, and per tile row below one TSQRT plus S chunks of
+    TSMQR per trailing column; FP64 splits update tasks in two from NB = 128
+    on, FP32 from NB = 192, and QR_OPT_SPLIT overrides both."""
+    def count(MT, NT, S):
+        c = 0
+        for k in range(min(MT, NT)):
+            c += 1 + (NT - k - 1) * S
+            c += (MT - k - 1) * (1 + (NT - k - 1) * S)
+        return c
+
+    assert L.qr_task_count(1000, 1000, 128, 8, 0) == count(8, 8, 2)
+    assert L.qr_task_count(1000, 1000, 128, 8, 1) == count(8, 8, 1)
+    assert L.qr_task_count(1000, 900, 64, 8, 0) == count(16, 15, 1)
+    assert L.qr_task_count(2000, 1000, 192, 16, 1) == count(11, 6, 2)
+    assert L.qr_task_count(2000, 1000, 384, 16, 0) == count(6, 3, 4)
+    assert L.qr_set_option(3, 3) == 0
+    try:
+        assert L.qr_task_count(1000, 1000, 64, 8, 0) == count(16, 16, 3)
+    finally:
+        assert L.qr_set_option(3, 0) == 0
