@@ -14,6 +14,9 @@ Contents:
   * ``tuning.py`` -- the paper's pruning rules (Properties 4.1, 4.2, 5.1,
     Heuristics 0/1/2, nearest-point interpolation) as plain Python loops.
   * ``mlp.py`` -- fp64 numpy forward/backward/Adam of the cost-model MLP.
+  * ``tile_apply.py`` -- Q^T of a flat-tree tile QR applied in NumPy from
+    stored factors (reflectors and T blocks): the large-N probe that checks
+    the GPU's stored factors independently of its Q-application kernels.
 
 The paper is Agullo, Dongarra, Nath, Tomov, "A Fully Empirical Autotuned
 Dense QR Factorization for Multicore Architectures" (INRIA RR-7526).

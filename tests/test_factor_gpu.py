@@ -282,3 +282,21 @@ def test_factor_fp32_flat_tree_budget(q, m, n, nb, ib):
     assert np.linalg.norm(np.triu(QtA[:n]) - R) / np.linalg.norm(R) <= 10 * n * u32
     if m > n:
         assert np.linalg.norm(QtA[n:]) / np.linalg.norm(R) <= 10 * n * u32
+
+
+@pytest.mark.parametrize("m,n,nb,ib", [(777, 600, 96, 24), (1000, 1000, 128, 8), (513, 300, 64, 7)])
+def test_stored_factors_applied_on_cpu(q, m, n, nb, ib):
+    """The GPU's stored factors (reflectors below R, T blocks), applied on
+    the CPU by an independent restatement of the tile updates
+    (oracle/tile_apply.py), take A to R over several panels and ragged
+    tiles; NB = 128 runs the FP64 update tasks as two column chunks."""
+    from oracle.tile_apply import tile_qt_apply
+    A = inputs.uniform_matrix(m, n, seed=m + 11 * n)
+    f = _gpu_factor(q, A, nb, ib)
+    F = f.A.cpu().numpy()
+    T = f.T.cpu().numpy()
+    QtA = tile_qt_apply(F, T, nb, ib, A)
+    R = np.triu(F[:n])
+    assert np.linalg.norm(QtA[:n] - R) / np.linalg.norm(R) <= 10 * n * 2.0 ** -53
+    if m > n:
+        assert np.linalg.norm(QtA[n:]) / np.linalg.norm(R) <= 10 * n * 2.0 ** -53

@@ -1,8 +1,9 @@
 """Parity at the benchmark's full size (FP64, N = 10000, the tuned (NB, IB)
 and ticket order that bench.py times), through properties the CPU can check
 entry by entry: R^T R = A^T A on sampled entries (invariant to R's row
-signs, independent of Q), and Q^T a_j = r_j on sampled columns through the
-separate Q-application kernel."""
+signs, independent of Q), Q^T a_j = r_j on sampled columns through the
+separate Q-application kernel, and Q^T (A Z) = R Z with Q^T applied on the
+CPU from the stored reflectors and T factors (oracle/tile_apply.py)."""
 import numpy as np
 import pytest
 
@@ -25,12 +26,18 @@ def q():
     return q
 
 
-def test_bench_size_factorization_properties(q):
+@pytest.fixture(scope="module")
+def fact(q):
     A = inputs.uniform_matrix(N, N, seed=SEED)
     nb, ib = q.qr_lookup(N, N, torch.float64)
     Ad = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
     f = q.qr_factor(Ad, nb, ib)
     torch.cuda.synchronize()
+    return A, f, nb, ib
+
+
+def test_bench_size_factorization_properties(q, fact):
+    A, f, nb, ib = fact
     assert f.status() == 0
     rng = np.random.default_rng(1)
     cn = np.linalg.norm(A, axis=0)
@@ -57,3 +64,17 @@ def test_bench_size_factorization_properties(q):
         r = np.zeros(N)
         r[: j + 1] = rcol(int(j))
         assert np.linalg.norm(QtA[:, c] - r) <= 10 * N * U * cn[j], j
+
+
+def test_bench_size_stored_factors_applied_on_cpu(q, fact):
+    """The stored tile factors (reflectors in A, T blocks) define an
+    orthogonal Q with Q^T A = R: applied on the CPU to A Z for random Z."""
+    from oracle.tile_apply import tile_qt_apply
+    A, f, nb, ib = fact
+    F = f.A.cpu().numpy()
+    T = f.T.cpu().numpy()
+    Z = np.random.default_rng(2).standard_normal((N, 3))
+    QtAZ = tile_qt_apply(F, T, nb, ib, A @ Z)
+    RZ = np.triu(F) @ Z
+    err = np.linalg.norm(QtAZ - RZ) / (np.linalg.norm(A) * np.linalg.norm(Z))
+    assert err <= 10 * N * U, err
