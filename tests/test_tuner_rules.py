@@ -178,3 +178,18 @@ def test_task_count_follows_the_column_split(L):
         assert L.qr_task_count(1000, 1000, 64, 8, 0) == count(16, 16, 3)
     finally:
         assert L.qr_set_option(3, 0) == 0
+
+
+def test_read_trace_decodes_records():
+    """read_trace unpacks the 32-byte trace records (task | type | SM, and
+    three globaltimer stamps made relative to the earliest ticket)."""
+    torch = pytest.importorskip("torch")
+    import paper_1102_5328_gb300 as q
+    recs = [(5, 3, 17, 1000, 1400, 2000), (0, 0, 151, 900, 950, 1500), (7, 5, 2, 1200, 1300, 1800)]
+    buf = torch.zeros((4, 4), dtype=torch.int64)
+    for r, (task, typ, sm, t0, t1, t2) in enumerate(recs):
+        buf[r, 0] = (sm << 48) | (typ << 40) | task
+        buf[r, 1], buf[r, 2], buf[r, 3] = t0, t1, t2
+    task, typ, sm, tt, tr, td = q.read_trace(buf, 3)
+    assert task.tolist() == [5, 0, 7] and typ.tolist() == [3, 0, 5] and sm.tolist() == [17, 151, 2]
+    assert tt.tolist() == [100, 0, 300] and tr.tolist() == [500, 50, 400] and td.tolist() == [1100, 600, 900]
