@@ -1,6 +1,9 @@
 """Plant plausible mistakes in a copy of the oracle (on the CPU) and check
-that the pins of test_oracle.py catch each one: a dropped term, a wrong
-sign convention, a wrong index and a wrong tau formula."""
+that the pins of test_oracle.py and test_oracle_checkers.py catch each one:
+in the factorization a dropped term, a wrong sign convention, a wrong index
+and a wrong tau formula; in the accuracy checks a dropped factor 2 on the
+off-diagonal terms of I - Q^T Q, a loop that skips the diagonal (of R, or of
+Q^T Q), a missing square root and a wrong normalisation."""
 import ctypes
 import os
 import shutil
@@ -11,6 +14,7 @@ import pytest
 
 import oracle
 from tests import test_oracle as pins
+from tests import test_oracle_checkers as cpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "qr_oracle.c")
 
@@ -21,6 +25,12 @@ MUTANTS = {
     "shifted_row_index": ("      a[0] -= w;\n      for (int64_t r = 0; r < len; ++r) a[r + 1] -= w * v[r];\n    }\n  }\n  return 0;\n}\n\n/* C <- Q^T C",
                           "      a[0] -= w;\n      for (int64_t r = 0; r < len; ++r) a[r] -= w * v[r];\n    }\n  }\n  return 0;\n}\n\n/* C <- Q^T C"),
     "wrong_tau": ("double tau = (beta - a) / beta;", "double tau = (beta - a) / a;"),
+    "fact_skips_diagonal": ("for (int64_t p = 0; p <= c; ++p) s -=", "for (int64_t p = 0; p < c; ++p) s -="),
+    "fact_unsquared_norm": ("return (double)(sqrtl(num) / sqrtl(den));", "return (double)(sqrtl(num) / den);"),
+    "orth_dropped_offdiag_2x": ("acc += (i == j) ? s * s : 2.0L * s * s;", "acc += s * s;"),
+    "orth_skips_diagonal": ("for (int64_t i = 0; i <= j; ++i) {\n      long double s = (i == j)",
+                            "for (int64_t i = 0; i < j; ++i) {\n      long double s = (i == j)"),
+    "orth_missing_sqrt": ("return (double)sqrtl(acc);", "return (double)acc;"),
 }
 
 PIN_TESTS = [
@@ -29,6 +39,11 @@ PIN_TESTS = [
     lambda: pins.test_rtr_equals_ata(),
     lambda: pins.test_against_long_double_mgs(8, 5),
     lambda: pins.test_backward_and_orthogonality(128, 128),
+    lambda: cpins.test_fact_residual_exact_rational(7, 4, 1),
+    lambda: cpins.test_fact_residual_single_entry(6, 6, 0),
+    lambda: cpins.test_orth_residual_exact_rational(6, 3, 1),
+    lambda: cpins.test_orth_residual_perturbed(6, 6, 0),
+    lambda: cpins.test_orth_residual_scaled_columns(),
 ]
 
 
