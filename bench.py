@@ -33,10 +33,12 @@ import numpy as np  # noqa: E402
 N_DEFAULT = 10000
 SEED = 10000
 
-# DRAM bytes (read + write) of one persistent_qr<double> launch, from one
-# ncu capture of the same configuration and kernel sources
-# (profiles/persistent_qr_fp64_n10000.md); None for any other configuration.
+# DRAM bytes (read + write) of one persistent_qr<double> launch, carried over
+# from one ncu capture of the same configuration and kernel sources
+# (profiles/persistent_qr_fp64_n10000.md), not measured by this run; None for
+# any other configuration.
 TRAFFIC_BYTES = {(10000, 10000, 128, 8): 57.57e9 + 41.40e9}
+TRAFFIC_SOURCE = "carried over: ncu capture in profiles/persistent_qr_fp64_n10000.md (same kernel sources)"
 
 
 def max_over_ranks(x, device="cuda"):
@@ -330,13 +332,13 @@ def run_step1(args):
     nb, ib = args.nb or 128, args.ib or 8
     prec = 1 if args.prec == "f32" else 0
     b = ctypes.c_int64()
-    q._lib.check(L.qr_step1_workspace(nb, prec, ctypes.byref(b)), "qr_step1_workspace")
+    q._lib.check(L.qr_step1_workspace(nb, prec, 0, ctypes.byref(b)), "qr_step1_workspace")
     work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
     s, g = ctypes.c_double(), ctypes.c_double()
     for _ in range(max(1, args.warmup)):
-        q._lib.check(L.qr_step1_time(nb, ib, prec, 3, ctypes.byref(s), ctypes.byref(g), ctypes.c_void_p(work.data_ptr()),
-                                     b.value, q._stream_ptr()), "qr_step1_time")
-    q._lib.check(L.qr_step1_time(nb, ib, prec, max(args.steps, 3), ctypes.byref(s), ctypes.byref(g),
+        q._lib.check(L.qr_step1_time(nb, ib, prec, 3, 0, ctypes.byref(s), ctypes.byref(g),
+                                     ctypes.c_void_p(work.data_ptr()), b.value, q._stream_ptr()), "qr_step1_time")
+    q._lib.check(L.qr_step1_time(nb, ib, prec, max(args.steps, 3), 0, ctypes.byref(s), ctypes.byref(g),
                                  ctypes.c_void_p(work.data_ptr()), b.value, q._stream_ptr()), "qr_step1_time")
     peak = q.qr_peak_fp64()
     line = {"workload": "Step-1 TSMQR batch, %s, NB=%d IB=%d" % (args.prec, nb, ib), "ms_per_launch": s.value * 1e3,
@@ -457,6 +459,8 @@ def main():
         "peak_measured_live": peak_live / 1e3, "frac_of_measured": achieved / (peak_live / 1e3),
         "traffic": TRAFFIC_BYTES.get((m, n, nb, ib)), "kernel_ms_avg": kavg,
     }
+    if roofline["traffic"] is not None:
+        roofline["traffic_source"] = TRAFFIC_SOURCE
 
     e2e = None
     if not args.no_e2e:
@@ -495,8 +499,9 @@ def main():
         cpu = {"value": g, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                "sample": "first %d Householder reflectors of the same N=%d matrix (%.1f s)" % (k, n, dt)}
 
-    # the tuner's own figures, from the committed install-time tuning run
-    # (measured by paper_1102_5328_gb300.tune / tune_eval, not in this timed region)
+    # the tuner's own figures: NOT measured by this run; copied from the
+    # committed install-time tuning campaign (paper_1102_5328_gb300.tune /
+    # tune_eval on a GB300), with the repetitions behind each figure
     tuning = None
     tpath = os.path.join(ROOT, "paper_1102_5328_gb300", "tuned", "gb300_fp64_reliability.json")
     if os.path.exists(tpath):
@@ -504,8 +509,10 @@ def main():
             tj = json.load(f)
         tuning = {k: tj.get(k) for k in ("autotuned_over_grid_best", "autotuned_over_grid_best_min",
                                         "optimum_found", "tuning_seconds", "full_grid_seconds",
-                                        "tuning_over_full_grid", "heuristic")}
-        tuning["source"] = "paper_1102_5328_gb300/tuned/gb300_fp64_reliability.json"
+                                        "full_grid_seconds_basis", "tuning_over_full_grid", "heuristic",
+                                        "es_reps", "pspayg_reps", "model")}
+        tuning = {k: v for k, v in tuning.items() if v is not None}
+        tuning["source"] = "committed: paper_1102_5328_gb300/tuned/gb300_fp64_reliability.json (not this run)"
 
     if rank == 0:
         line = {

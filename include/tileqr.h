@@ -35,9 +35,13 @@
 extern "C" {
 #endif
 
-/* Element types of the working precision (prec arguments). */
+/* Element types of the working precision (prec arguments). QR_PREC_TF32 and
+ * QR_PREC_BF16X3 keep FP32 storage and run the factorization's UNMQR/TSMQR
+ * products on the tensor cores (qr_factor_mixed_s, qr_solve_ls). */
 #define QR_PREC_F64 0
 #define QR_PREC_F32 1
+#define QR_PREC_TF32 2   /* one TF32 product per update, FP32 accumulation */
+#define QR_PREC_BF16X3 3 /* three BF16 products of split operands (hi*hi + hi*lo + lo*hi), FP32 accumulation */
 
 /* Device status bits (qr_status). */
 #define QR_DEV_TIMEOUT   1 /* a scheduler dependency wait ran out of time */
@@ -85,6 +89,23 @@ int qr_factor_d(int64_t m, int64_t n, double *d_A, int64_t lda, int nb, int ib, 
                 void *d_scratch, int64_t scratch_bytes, void *stream);
 int qr_factor_s(int64_t m, int64_t n, float *d_A, int64_t lda, int nb, int ib, float *d_T,
                 void *d_scratch, int64_t scratch_bytes, void *stream);
+
+/*
+ * qr_factor_mixed_s -- FP32 tile QR whose trailing-update products (UNMQR and
+ * TSMQR, the paper's DLARFB and DSSRFB) run at precision prec:
+ * QR_PREC_F32 (FP32 cores, the same as qr_factor_s / qr_factor_p_s),
+ * QR_PREC_TF32 or QR_PREC_BF16X3 (warp-level tensor-core products, FP32
+ * accumulation; tasks with more than 512 rows, IB > 32 or that do not fit
+ * the shared-memory budget, and the triangle-on-triangle TTMQR updates, stay
+ * on the FP32 cores). The panel kernels (norms, beta, tau in FP64; V and T)
+ * are those of qr_factor_s. p >= 1 panel domains (1 = flat tree, as
+ * qr_factor_s; p > 1 as qr_factor_p_s). Buffers sized by qr_workspace
+ * (p = 1) or qr_workspace_p with QR_PREC_F32; output layout as qr_factor_s,
+ * so qr_apply_qt_s / qr_apply_qt_p_s apply its Q. -7: bad p, -8: bad prec;
+ * otherwise the return codes of qr_factor_s (p = 1) or qr_factor_p_s.
+ */
+int qr_factor_mixed_s(int64_t m, int64_t n, float *d_A, int64_t lda, int nb, int ib, int p, int prec, float *d_T,
+                      void *d_scratch, int64_t scratch_bytes, void *stream);
 
 /*
  * qr_apply_qt_d / qr_apply_qt_s -- C <- Q^T C (trans = 1) or C <- Q C
@@ -167,18 +188,24 @@ int qr_apply_qt_p_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64_
  * Its scratch is a fixed device array of QR_NOALLOC_SCRATCH_BYTES bytes
  * compiled into the library; every GPU that loads the library holds it until
  * the process exits. Problems whose scratch (as qr_workspace would report)
- * exceeds that size are rejected with -1 before anything is queued (for
- * example 1024 x 1024 with nb = 64 fits; 4096 x 4096 does not).
+ * exceeds that size are rejected with QR_NOALLOC_TOO_LARGE before anything
+ * is queued (for example 1024 x 1024 with nb = 64 fits; 4096 x 4096 does
+ * not); that code lies outside the -1..-9 range of argument errors.
  * Arguments as qr_factor_d; d_A and d_T are the caller's input/output.
+ * nb = 0 takes (nb, ib) from the tuning table as qr_factor_d does, but always
+ * runs the flat tree: for tall-skinny shapes the table's pair was tuned
+ * together with p > 1 panel domains, so it may not be the fastest here.
  * d_status (device int, may be NULL) receives the QR_DEV_* bits of this call.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
+ * The first call in each CUDA context (each device, and again after
+ * cudaDeviceReset) looks up the array's device address
+ * (cudaGetSymbolAddress) with that context current; make that first call
  * before any stream capture. All calls share the one array: calls that
  * overlap on the GPU (concurrent streams, several host threads) race and
  * corrupt each other -- serialise them. Each call clears the status word,
  * ticket and counters it needs; tasks run in the DAG's program order.
  */
 #define QR_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define QR_NOALLOC_TOO_LARGE (-100)
 int qr_factor_d_noalloc(int64_t m, int64_t n, double *d_A, int64_t lda, int nb, int ib, double *d_T,
                         int *d_status, void *stream);
 
@@ -310,9 +337,9 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t l
 /*
  * qr_tune -- install-time tuning (Sec. 6: "make autotune", then an instant
  * decision at call time). Shapes (ms[i], ns[i]), nshapes >= 1.
- * mode 0 (PSPAYG): Step 1 = time the TSMQR kernel (the paper's DSSRFB) for
- *   every (NB, IB) of the grid NB in {64..512 step 32}, IB | NB,
- *   8 <= IB <= NB/2 (119 pairs), 50 launches each, "No Flush" (Sec. 4);
+ * mode bit 0 = 0 (PSPAYG): Step 1 = time the TSMQR kernel (the paper's
+ *   DSSRFB) for every (NB, IB) of the grid NB in {64..512 step 32}, IB | NB,
+ *   8 <= IB <= NB/2 (119 pairs), up to 50 launches each (Sec. 4);
  *   Property 4.1 (best IB per NB), Property 4.2 (upper convex hull) and
  *   Heuristic `heuristic` (0, 1 or 2; 2 is the paper's default) preselect at
  *   most 8 pairs; Step 2 = time qr_factor for the survivors at every shape,
@@ -322,18 +349,53 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t l
  *   is then timed with p = 2, 4, ... panel domains (qr_factor_p_*; at most
  *   64 and 2 MT/NT), the paper's third tunable for such matrices; the
  *   table records the best p (1 = flat tree).
- * mode 1 (exhaustive search, ES): Step 2 over the whole grid, no pruning.
+ * mode bit 0 = 1 (exhaustive search, ES): Step 2 over the whole grid, no
+ *   pruning.
+ * mode bit 1 (value 2): Step 1 as MultCallFlushLRU -- each launch works on
+ *   its own copy of the operands, taken in turn from enough copies that its
+ *   data was last touched two L2 capacities ago (the paper reports "No
+ *   Flush", where every launch reuses the same data, and leaves the flushing
+ *   variants out of scope, Sec. 4). Logged as kind 5 instead of 1.
+ * use_model = k in [1, 8] (0 = off; this library's addition, the paper
+ *   tunes without a model): the learned cost model (qr_mlp_*), fitted on
+ *   the GPU to the Step-2 timings of the orders already done (features
+ *   log m, log n, NB/512, IB/256; target log seconds), ranks the survivors
+ *   of each order from the third one on, and only the k it ranks fastest are
+ *   timed; the search goes further down the ranking while the last pair
+ *   timed is the fastest so far, and times every survivor when a prediction
+ *   of a timed pair is off by more than a factor e^0.25. Measurements always
+ *   decide; a survivor left untimed is not pruned. The final model, fitted
+ *   to all Step-2 timings, is saved in the table ("model") and answers
+ *   qr_model_propose. Predictions are logged as kind 4.
  * prec: QR_PREC_F64 / QR_PREC_F32. table_path (may be NULL/""): JSON decision
  * table written at the end; it also becomes the in-process table used by
  * nb = 0. log_path (may be NULL/""): JSONL of every measurement, appended;
  * measurements already in it are reused, so an interrupted run resumes.
  * d_work (work_bytes >= qr_tune_workspace): device scratch owned by the
- * caller. seconds_out[4] (may be NULL): total, Step-1 and Step-2 wall
- * seconds, and the number of factorizations timed in this call. Synchronous.
+ * caller; its first QR_MODEL_WORK_BYTES hold the model's buffers.
+ * seconds_out[6] (may be NULL): total, Step-1 and Step-2 wall seconds, the
+ * number of factorizations timed in this call, the seconds spent fitting
+ * and evaluating the model, and the orders where the model's check fell
+ * back to timing every survivor. Synchronous. Errors: -4 heuristic, -5 mode,
+ * -6 use_model, -7 reps, -8 prec, -9 table not writable, -11 no d_work,
+ * -12 d_work too small.
  */
-int qr_tune(const int64_t *ms, const int64_t *ns, int nshapes, int heuristic, int mode, int reps, int prec,
-            const char *table_path, const char *log_path, void *d_work, int64_t work_bytes,
+#define QR_MODEL_WORK_BYTES (4ll << 20)
+int qr_tune(const int64_t *ms, const int64_t *ns, int nshapes, int heuristic, int mode, int use_model, int reps,
+            int prec, const char *table_path, const char *log_path, void *d_work, int64_t work_bytes,
             double *seconds_out, void *stream);
+
+/*
+ * qr_model_propose -- (nb, ib) for an untuned shape m x n from the learned
+ * cost model saved by the last qr_tune with use_model > 0 (or loaded with
+ * its table by qr_load_table): the pair of the model's candidate set (the
+ * tuner's preselected pairs) with the least predicted time, which goes to
+ * *seconds (may be NULL). d_work: device scratch of at least
+ * QR_MODEL_WORK_BYTES. Synchronous. Returns 1 when no model is loaded for
+ * prec (nothing written), -8 for a d_work that is too small.
+ */
+int qr_model_propose(int64_t m, int64_t n, int prec, int *nb, int *ib, double *seconds, void *d_work,
+                     int64_t work_bytes, void *stream);
 
 /* qr_tune_workspace -- device bytes qr_tune needs for shapes up to max_m x max_n. */
 int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t *bytes);
@@ -374,14 +436,17 @@ int64_t qr_tune_nearest(int64_t value, const int64_t *grid, int ngrid);
 /*
  * qr_step1_workspace / qr_step1_time -- the Step-1 kernel benchmark of Sec. 4
  * for one (nb, ib): `launches` back-to-back launches of a batch of
- * 2 x (SM count) independent TSMQR tile tasks (same data every launch:
- * "No Flush"), timed with CUDA events on `stream`; synchronous.
+ * 2 x (SM count) independent TSMQR tile tasks, timed with CUDA events on
+ * `stream`; synchronous. flush = 0: "No Flush" (same data every launch, the
+ * paper's reported mode); flush = 1: MultCallFlushLRU (launch l uses
+ * operand copy l mod c, with c copies covering at least two L2 capacities
+ * plus one copy, at least 2: each launch reads its operands from HBM).
  * launches <= 0 picks the count from one timed launch: enough launches for
  * about 30 ms, at least 3 and at most the paper's 50.
  * *seconds_per_launch, and *gflops (may be NULL) = batch x 4 NB^3 / time.
  */
-int qr_step1_workspace(int nb, int prec, int64_t *bytes);
-int qr_step1_time(int nb, int ib, int prec, int launches, double *seconds_per_launch, double *gflops,
+int qr_step1_workspace(int nb, int prec, int flush, int64_t *bytes);
+int qr_step1_time(int nb, int ib, int prec, int launches, int flush, double *seconds_per_launch, double *gflops,
                   void *d_work, int64_t work_bytes, void *stream);
 
 /*

@@ -20,6 +20,8 @@ from . import _lib
 
 QR_PREC_F64 = 0
 QR_PREC_F32 = 1
+QR_PREC_TF32 = 2
+QR_PREC_BF16X3 = 3
 QR_DEV_TIMEOUT = 1
 QR_DEV_NONFINITE = 2
 QR_OPT_WAIT_TIMEOUT_US = 1

@@ -67,16 +67,19 @@ SIGNATURES = [
                                   c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     ("qr_tune_payg", c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_dbl), ctypes.POINTER(c_int)]),
     ("qr_tune_nearest", c_i64, [c_i64, ctypes.POINTER(c_i64), c_int]),
-    ("qr_step1_workspace", c_int, [c_int, c_int, ctypes.POINTER(c_i64)]),
-    ("qr_step1_time", c_int, [c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_i64,
-                              c_vp]),
+    ("qr_step1_workspace", c_int, [c_int, c_int, c_int, ctypes.POINTER(c_i64)]),
+    ("qr_step1_time", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp,
+                              c_i64, c_vp]),
     ("qr_tune_workspace", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_i64)]),
     ("qr_time_factor", c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl),
                                c_vp, c_i64, c_vp]),
     ("qr_time_factor_p", c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_dbl),
                                  ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
-    ("qr_tune", c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_int, c_int, c_int, c_int, c_int,
+    ("qr_tune", c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_int, c_int, c_int, c_int, c_int, c_int,
                         ctypes.c_char_p, ctypes.c_char_p, c_vp, c_i64, ctypes.POINTER(c_dbl), c_vp]),
+    ("qr_factor_mixed_s", c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_int, c_vp, c_vp, c_i64, c_vp]),
+    ("qr_model_propose", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                 ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
     ("qr_peak_fp64", c_int, [ctypes.POINTER(c_dbl), c_vp]),
 ]
 

@@ -860,21 +860,46 @@ __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, 
   }
 }
 
+}  // namespace tqr
+
+#include "tc_update.cuh"
+
+namespace tqr {
+
 // UNMQR: C <- Q^T C for the GEQRT factors (V in the diagonal tile, rows x
-// nref reflectors, T IB x nref), columns [c0, c1) of C.
+// nref reflectors, T IB x nref), columns [c0, c1) of C. tc (FP32 tiles
+// only): TC_TF32 / TC_BF16X3 run the products on the tensor cores
+// (apply_qt_mma), TC_NONE on the FP32/FP64 cores.
 template <typename S>
 __device__ void unmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C, int ldc, int c0,
-                      int c1, const Smem<S>& sm) {
+                      int c1, const Smem<S>& sm, int tc = TC_NONE) {
+  if constexpr (sizeof(S) == 4) {
+    if (tc == TC_TF32 && apply_qt_mma<TC_TF32, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0, c1,
+                                                      sm.vs))
+      return;
+    if (tc == TC_BF16X3 && apply_qt_mma<TC_BF16X3, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0,
+                                                          c1, sm.vs))
+      return;
+  }
   apply_qt<S, false>(V, ldv, T, IB, false, 0, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm);
 }
 
 // TSMQR: [C1; C2] <- Q^T [C1; C2] for the TSQRT factors (V rows x nref in
 // the bottom tile, T IB x nref); C1 the top tile, C2 (rows) the bottom one.
 // tri = true is TTMQR: V holds triangle-on-triangle reflectors (upper
-// triangular), so only the first min(rows, nref) rows of C2 change.
+// triangular), so only the first min(rows, nref) rows of C2 change (always
+// on the FP32/FP64 cores). tc as for unmqr.
 template <typename S>
 __device__ void tsmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C1, int ldc1, S* C2,
-                      int ldc2, int c0, int c1, const Smem<S>& sm, bool tri = false) {
+                      int ldc2, int c0, int c1, const Smem<S>& sm, bool tri = false, int tc = TC_NONE) {
+  if constexpr (sizeof(S) == 4) {
+    if (!tri && tc == TC_TF32 &&
+        apply_qt_mma<TC_TF32, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs))
+      return;
+    if (!tri && tc == TC_BF16X3 &&
+        apply_qt_mma<TC_BF16X3, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs))
+      return;
+  }
   apply_qt<S, true>(V, ldv, T, IB, false, 0, nref, IB, C1, ldc1, C2, ldc2, tri ? min(rows, nref) : rows, c0, c1,
                     sm, tri);
 }

@@ -9,6 +9,7 @@
 // DAG, which pulls panel tasks of later steps forward - a look-ahead). A task
 // waits on per-tile progress counters (acquire loads with a time limit), runs
 // on its CTA, and publishes its tiles with a release increment.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -263,6 +264,7 @@ struct FactorArgs {
   uint64_t timeout_ns;
   TraceRec* trace;
   int64_t trace_cap;
+  int tc;  // TC_* precision of the UNMQR/TSMQR products (FP32 tiles)
 };
 
 template <typename S>
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr(FactorArgs<S> a) {
       case TASK_UNMQR: {
         const int cj = cols_of(j);
         const int c0 = (int)((int64_t)sch * cj / Sp), c1 = (int)((int64_t)(sch + 1) * cj / Sp);
-        unmqr<S>(tile(k, k), NB, tfac(k, k), a.IB, rk, ck, tile(k, j), NB, c0, c1, sm);
+        unmqr<S>(tile(k, k), NB, tfac(k, k), a.IB, rk, ck, tile(k, j), NB, c0, c1, sm, a.tc);
         break;
       }
       case TASK_TSQRT:
@@ -332,7 +334,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr(FactorArgs<S> a) {
       default: {
         const int cj = cols_of(j);
         const int c0 = (int)((int64_t)sch * cj / Sp), c1 = (int)((int64_t)(sch + 1) * cj / Sp);
-        tsmqr<S>(tile(i, k), NB, tfac(i, k), a.IB, rows_of(i), ck, tile(k, j), NB, tile(i, j), NB, c0, c1, sm);
+        tsmqr<S>(tile(i, k), NB, tfac(i, k), a.IB, rows_of(i), ck, tile(k, j), NB, tile(i, j), NB, c0, c1, sm,
+                 false, a.tc);
         break;
       }
     }
@@ -383,7 +386,7 @@ int persistent_grid(int* grid_out) {
 
 template <typename S>
 int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, void* scratch,
-                int64_t scratch_bytes, void* stream) {
+                int64_t scratch_bytes, void* stream, int tc = TC_NONE) {
   if (m < 0) return -1;
   if (n < 0 || n > m) return -2;
   if (!A && m * n > 0) return -3;
@@ -434,6 +437,7 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
   fa.tasks = dtasks; fa.ntasks = ntasks; fa.cnt = cnt; fa.ctl = ctl;
   fa.timeout_ns = (uint64_t)g_wait_timeout_us * 1000ull;
   fa.trace = (TraceRec*)g_trace.load(); fa.trace_cap = g_trace_cap.load();
+  fa.tc = tc;
   if (g_record) {
     if (!g_ev[0]) {
       if ((e = cudaEventCreate(&g_ev[0])) != cudaSuccess) return (int)e;
@@ -461,8 +465,67 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
 // device, on the first call made with that device current.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[QR_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+// The array's device address belongs to one CUDA context. It is looked up
+// once per context and cached under the context's unique id (cuCtxGetId,
+// reached through the runtime's driver entry points, so the library does not
+// link libcuda): a context created anew on the same device, for instance
+// after cudaDeviceReset, gets a fresh lookup instead of a stale address.
+struct NoallocSlot {
+  unsigned long long ctx_id;
+  void* ptr;
+};
+constexpr int kNoallocSlots = 64;
+NoallocSlot g_noalloc_slot[kNoallocSlots] = {};
+int g_noalloc_next = 0;
+
+typedef CUresult(CUDAAPI* CtxGetCurrentFn)(CUcontext*);
+typedef CUresult(CUDAAPI* CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Id of the context current on this thread; false if none is current (the
+// runtime makes its primary context current on its first device call).
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_cur || !get_id) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f)
+      return false;
+    get_cur = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f)
+      return false;
+    get_id = (CtxGetIdFn)f;
+  }
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_noalloc_scratch in the current context (0 or a CUDA
+// error code).
+int noalloc_scratch_address(void** out) {
+  unsigned long long id = 0;
+  if (current_context_id(&id)) {
+    for (int i = 0; i < kNoallocSlots; ++i)
+      if (g_noalloc_slot[i].ptr && g_noalloc_slot[i].ctx_id == id) {
+        *out = g_noalloc_slot[i].ptr;
+        return 0;
+      }
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return (int)e;
+  // the lookup has made the runtime's context current if none was
+  if (current_context_id(&id)) {
+    g_noalloc_slot[g_noalloc_next] = NoallocSlot{id, p};
+    g_noalloc_next = (g_noalloc_next + 1) % kNoallocSlots;
+  }
+  *out = p;
+  return 0;
+}
 
 // Program (k-major) order of the flat-tree DAG, written by the device: one
 // thread per elimination step, each computing its own offset.
@@ -501,19 +564,13 @@ int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, in
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lock(g_mu);
   const Layout L = make_layout(m, n, nb, ib, sizeof(double));
-  if (L.bytes > (size_t)QR_NOALLOC_SCRATCH_BYTES) return -1;  // too large for the fixed scratch
-  if (L.MT > 65535 || L.NT > 65535) return -1;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return (int)e;
-  if (dev < 0 || dev >= kMaxDevices) return (int)cudaErrorInvalidDevice;
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return (int)e;
-    g_noalloc_ptr[dev] = p;
-  }
-  char* base = (char*)g_noalloc_ptr[dev];
+  // too large for the fixed scratch (this bound also keeps MT, NT small)
+  if (L.bytes > (size_t)QR_NOALLOC_SCRATCH_BYTES || L.MT > 65535 || L.NT > 65535) return QR_NOALLOC_TOO_LARGE;
+  void* scratch = nullptr;
+  int rc0 = noalloc_scratch_address(&scratch);
+  if (rc0) return rc0;
+  cudaError_t e;
+  char* base = (char*)scratch;
   DevCtl* ctl = (DevCtl*)base;
   unsigned* cnt = (unsigned*)(base + L.off_cnt);
   uint64_t* dtasks = (uint64_t*)(base + L.off_tasks);
@@ -533,6 +590,7 @@ int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, in
   fa.tasks = dtasks; fa.ntasks = L.ntasks; fa.cnt = cnt; fa.ctl = ctl;
   fa.timeout_ns = (uint64_t)g_wait_timeout_us * 1000ull;
   fa.trace = (TraceRec*)g_trace.load(); fa.trace_cap = g_trace_cap.load();
+  fa.tc = TC_NONE;
   persistent_qr<double><<<grid, NTHREADS, smem_elems<double>() * sizeof(double), st>>>(fa);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   tiles_to_cm<double><<<1184, 256, 0, st>>>(W, A, lda, m, n, nb, L.MT);
@@ -600,6 +658,20 @@ int qr_factor_d(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, do
 int qr_factor_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, float* T, void* scratch,
                 int64_t scratch_bytes, void* stream) {
   return factor_impl<float>(m, n, A, lda, nb, ib, T, scratch, scratch_bytes, stream);
+}
+
+int qr_factor_mixed_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, int p, int prec, float* T,
+                      void* scratch, int64_t scratch_bytes, void* stream) {
+  int tc;
+  switch (prec) {
+    case QR_PREC_F32: tc = TC_NONE; break;
+    case QR_PREC_TF32: tc = TC_TF32; break;
+    case QR_PREC_BF16X3: tc = TC_BF16X3; break;
+    default: return -8;
+  }
+  if (p < 1 || p > 4096) return -7;
+  if (p == 1) return factor_impl<float>(m, n, A, lda, nb, ib, T, scratch, scratch_bytes, stream, tc);
+  return qr_factor_p_tc_s(m, n, A, lda, nb, ib, p, T, scratch, scratch_bytes, stream, tc);
 }
 
 int qr_factor_d_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, int* d_status,

@@ -374,6 +374,7 @@ struct DagArgs {
   uint64_t timeout_ns;
   TraceRec* trace;
   int64_t trace_cap;
+  int tc;  // TC_* precision of the UNMQR/TSMQR products (FP32 tiles)
 };
 
 template <typename S>
@@ -436,12 +437,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr_dag(DagArgs<S> a) {
     }
     switch (type) {
       case D_GEQRT: geqrt<S>(tile(h, k), NB, rows_of(h), ck, a.IB, t1(h, k), sm, &a.ctl->status); break;
-      case D_UNMQR: unmqr<S>(tile(h, k), NB, t1(h, k), a.IB, rows_of(h), ck, tile(h, j), NB, c0, c1, sm); break;
+      case D_UNMQR:
+        unmqr<S>(tile(h, k), NB, t1(h, k), a.IB, rows_of(h), ck, tile(h, j), NB, c0, c1, sm, a.tc);
+        break;
       case D_TSQRT:
         tsqrt<S>(tile(h, k), NB, tile(i, k), NB, rows_of(i), ck, a.IB, t1(i, k), sm, &a.ctl->status, false);
         break;
       case D_TSMQR:
-        tsmqr<S>(tile(i, k), NB, t1(i, k), a.IB, rows_of(i), ck, tile(h, j), NB, tile(i, j), NB, c0, c1, sm, false);
+        tsmqr<S>(tile(i, k), NB, t1(i, k), a.IB, rows_of(i), ck, tile(h, j), NB, tile(i, j), NB, c0, c1, sm, false,
+                 a.tc);
         break;
       case D_TTQRT:
         tsqrt<S>(tile(h, k), NB, tile(i, k), NB, rows_of(i), ck, a.IB, t2(i, k), sm, &a.ctl->status, true);
@@ -477,7 +481,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr_dag(DagArgs<S> a) {
 
 template <typename S>
 int factor_p_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, int p, S* T, void* scratch,
-                  int64_t scratch_bytes, void* stream) {
+                  int64_t scratch_bytes, void* stream, int tc = TC_NONE) {
   if (m < 0) return -1;
   if (n < 0 || n > m) return -2;
   if (!A && m * n > 0) return -3;
@@ -528,11 +532,12 @@ int factor_p_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, int p
   da.timeout_ns = (uint64_t)qr_get_option(QR_OPT_WAIT_TIMEOUT_US) * 1000ull;
   {
     void* tb = nullptr;
-    int64_t tc = 0;
-    qr_trace_target(&tb, &tc);
+    int64_t tcap = 0;
+    qr_trace_target(&tb, &tcap);
     da.trace = (TraceRec*)tb;
-    da.trace_cap = tc;
+    da.trace_cap = tcap;
   }
+  da.tc = sizeof(S) == 4 ? tc : TC_NONE;
   persistent_qr_dag<S><<<grid, NTHREADS, smem, st>>>(da);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   tiles_to_cm<S><<<1184, 256, 0, st>>>(W, A, lda, m, n, nb, L.MT);
@@ -798,3 +803,8 @@ int qr_apply_qt_p_s(int64_t m, int64_t n, int64_t nrhs, const float* A, int64_t 
 }
 
 }  // extern "C"
+
+int qr_factor_p_tc_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, int p, float* T, void* scratch,
+                     int64_t scratch_bytes, void* stream, int tc) {
+  return factor_p_impl<float>(m, n, A, lda, nb, ib, p, T, scratch, scratch_bytes, stream, tc);
+}

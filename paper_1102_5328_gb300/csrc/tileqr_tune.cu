@@ -13,9 +13,14 @@
 // (Sec. 5.1). The decision table is written to JSON and every measurement is
 // appended to a JSONL log, which a later run reads to skip what is measured.
 //
-// Optionally a small MLP cost model (tileqr_mlp.cu), trained on the timings
-// gathered so far, ranks the survivors at each new N; only the ones it ranks
-// near the top are measured, and the measurement always decides.
+// Optionally (use_model = k > 0) a small MLP cost model (tileqr_mlp.cu),
+// trained on the Step-2 timings gathered so far, ranks the survivors at each
+// new order from the third one on; only the k it ranks best are measured
+// (more when the ranking or the predictions prove unreliable), and the
+// measurement always decides. The final model, fitted to every Step-2
+// timing, is saved with the table and proposes pairs for untuned shapes.
+// Step 1 can also run as MultCallFlushLRU (every launch on operands that are
+// not in L2), the variant the paper leaves out of scope (Sec. 4).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -150,7 +155,7 @@ bool write_table(const char* path, int prec, const std::vector<Entry>& t, const 
   return true;
 }
 
-bool read_table(const char* path, int* prec, std::vector<Entry>* t) {
+bool read_table(const char* path, int* prec, std::vector<Entry>* t, std::string* text = nullptr) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
   std::string s;
@@ -159,6 +164,7 @@ bool read_table(const char* path, int* prec, std::vector<Entry>* t) {
   while ((r = fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, r);
   fclose(f);
   *prec = (s.find("\"prec\": \"fp32\"") != std::string::npos) ? 1 : 0;
+  if (text) *text = s;
   size_t p = s.find("\"entries\"");
   if (p == std::string::npos) return false;
   t->clear();
@@ -220,22 +226,76 @@ int64_t step1_bytes(int nb, int nbatch, size_t esz) {
   return (int64_t)((2 + 2 * (size_t)nbatch) * nb * nb * esz) + 4096;
 }
 
+int64_t l2_bytes() {
+  int dev = 0, l2 = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+  return l2 > 0 ? l2 : (128ll << 20);
+}
+
+// MultCallFlushLRU: every launch works on its own copy of the operands
+// (V, T and the tile pairs), the copies taken in turn, and there are enough
+// of them that the ones a launch reads were last touched more than two L2
+// capacities of traffic ago: each launch finds its data in HBM, not in L2.
+int step1_flush_sets(int nb, int nbatch, size_t esz) {
+  const int64_t set = step1_bytes(nb, nbatch, esz);
+  return (int)std::max<int64_t>(2, (2 * l2_bytes() + set - 1) / set + 1);
+}
+
+int64_t step1_flush_bytes(int nb, int nbatch, size_t esz) {
+  return (int64_t)step1_flush_sets(nb, nbatch, esz) * step1_bytes(nb, nbatch, esz);
+}
+
+// Extra workspace of the flushed Step 1 over the plain one, largest over the grid.
+int64_t step1_flush_extra(size_t esz) {
+  int64_t best = 0;
+  const int nbatch = 2 * sm_count();
+  for (int nb = 64; nb <= 512; nb += 32)
+    best = std::max(best, step1_flush_bytes(nb, nbatch, esz) - step1_bytes(512, nbatch, esz));
+  return best;
+}
+
+// One operand set of the Step-1 batch: V, T, then the nbatch tile pairs.
 template <typename S>
-int step1_time(int nb, int ib, int nbatch, int launches, double* sec, void* work, int64_t wbytes,
-               cudaStream_t st) {
-  if (step1_bytes(nb, nbatch, sizeof(S)) > wbytes) return -7;
+struct Step1Set {
+  S *V, *T, *C1, *C2;
+};
+template <typename S>
+Step1Set<S> step1_set(void* work, int nb, int nbatch, int k) {
   const size_t te = (size_t)nb * nb;
-  S* V = (S*)work;
-  S* T = V + te;
-  S* C1 = T + te;
-  S* C2 = C1 + (size_t)nbatch * te;
-  fill_uniform<S><<<1024, 256, 0, st>>>(V, (int64_t)te, 11, -0.05, 0.05);
-  fill_uniform<S><<<1024, 256, 0, st>>>(T, (int64_t)te, 12, 0.0, 0.05);
-  fill_uniform<S><<<1024, 256, 0, st>>>(C1, (int64_t)(2 * nbatch * te), 13, -0.5, 0.5);
+  Step1Set<S> o;
+  o.V = (S*)((char*)work + (size_t)k * step1_bytes(nb, nbatch, sizeof(S)));
+  o.T = o.V + te;
+  o.C1 = o.T + te;
+  o.C2 = o.C1 + (size_t)nbatch * te;
+  return o;
+}
+
+// flush = 0: "No Flush", every launch on the same data (the mode the paper
+// reports, Sec. 4). flush = 1: MultCallFlushLRU, launch l on operand set
+// l mod nsets (step1_flush_sets), so its data is never in L2.
+template <typename S>
+int step1_time(int nb, int ib, int nbatch, int launches, int flush, double* sec, void* work, int64_t wbytes,
+               cudaStream_t st) {
+  const int nsets = flush ? step1_flush_sets(nb, nbatch, sizeof(S)) : 1;
+  if ((int64_t)nsets * step1_bytes(nb, nbatch, sizeof(S)) > wbytes) return -7;
+  const size_t te = (size_t)nb * nb;
+  for (int k = 0; k < nsets; ++k) {
+    const Step1Set<S> o = step1_set<S>(work, nb, nbatch, k);
+    fill_uniform<S><<<1024, 256, 0, st>>>(o.V, (int64_t)te, 11 + 16 * k, -0.05, 0.05);
+    fill_uniform<S><<<1024, 256, 0, st>>>(o.T, (int64_t)te, 12 + 16 * k, 0.0, 0.05);
+    fill_uniform<S><<<1024, 256, 0, st>>>(o.C1, (int64_t)(2 * nbatch * te), 13 + 16 * k, -0.5, 0.5);
+  }
   const size_t smem = smem_elems<S>() * sizeof(S);
   cudaError_t e = cudaFuncSetAttribute(tsmqr_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(V, T, C1, C2, nb, ib);  // warm-up
+  int cur = 0;
+  auto launch = [&]() {
+    const Step1Set<S> o = step1_set<S>(work, nb, nbatch, cur);
+    cur = (cur + 1) % nsets;
+    tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(o.V, o.T, o.C1, o.C2, nb, ib);
+  };
+  launch();  // warm-up
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -243,7 +303,7 @@ int step1_time(int nb, int ib, int nbatch, int launches, double* sec, void* work
     // adaptive count: time one launch, then take as many as fill ~30 ms
     // (at least 3, at most the paper's 50)
     cudaEventRecord(e0, st);
-    tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(V, T, C1, C2, nb, ib);
+    launch();
     cudaEventRecord(e1, st);
     e = cudaEventSynchronize(e1);
     float ms1 = 1.f;
@@ -253,7 +313,7 @@ int step1_time(int nb, int ib, int nbatch, int launches, double* sec, void* work
     launches = std::max(3, std::min(50, launches));
   }
   cudaEventRecord(e0, st);
-  for (int l = 0; l < launches; ++l) tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(V, T, C1, C2, nb, ib);
+  for (int l = 0; l < launches; ++l) launch();
   cudaEventRecord(e1, st);
   e = cudaEventSynchronize(e1);
   float ms = 0;
@@ -320,9 +380,227 @@ int time_factor(int64_t m, int64_t n, int nb, int ib, int pd, int reps, void* wo
 
 double qr_flops_d(int64_t m, int64_t n) { return 2.0 * m * (double)n * n - 2.0 * (double)n * n * n / 3.0; }
 
+// --- the learned cost model inside the search --------------------------------
+// The tuner's own Step-2 timings train the MLP of tileqr_mlp.cu (features
+// (log m, log n, NB/512, IB/256), standardized over the training set; target
+// log seconds, centred). Its device buffers sit at the start of the tuner's
+// workspace (kModelBytes); the factorization timings use the rest.
+constexpr int kModelCap = 4096;  // training samples at most
+constexpr int64_t kModelBytes = QR_MODEL_WORK_BYTES;
+constexpr int kModelSteps = 3000;
+constexpr float kModelLr = 1e-3f;
+constexpr double kModelTrust = 0.25;  // |log t_measured - log t_predicted| allowed before falling back
+
+struct Model {
+  bool ok = false;
+  float mean[4] = {0, 0, 0, 0}, sd[4] = {1, 1, 1, 1};
+  float ymean = 0.f;
+  std::vector<float> params;
+  std::vector<std::pair<int, int>> pairs;  // candidate (NB, IB) pairs it was trained on
+};
+Model g_model[2];  // [0] fp64, [1] fp32 (guarded by g_tmu)
+
+struct Sample {
+  int64_t m, n;
+  int nb, ib;
+  double sec;
+};
+
+void raw_features(int64_t m, int64_t n, int nb, int ib, float* f) {
+  f[0] = (float)std::log((double)m);
+  f[1] = (float)std::log((double)n);
+  f[2] = (float)(nb / 512.0);
+  f[3] = (float)(ib / 256.0);
+}
+
+// Initial weights: each Linear(in, out) draws W and b uniform in
+// [-1/sqrt(in), 1/sqrt(in)] from a SplitMix64 stream (fixed seed).
+std::vector<float> model_init(uint64_t seed) {
+  std::vector<float> p(QR_MLP_NPARAMS);
+  const int fin[3] = {4, 64, 64}, fout[3] = {64, 64, 1};
+  uint64_t x = seed;
+  auto next = [&x]() {
+    x += 0x9E3779B97F4A7C15ull;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  size_t o = 0;
+  for (int l = 0; l < 3; ++l) {
+    const double b = 1.0 / std::sqrt((double)fin[l]);
+    for (int e = 0; e < fin[l] * fout[l] + fout[l]; ++e) p[o++] = (float)(-b + 2.0 * b * next());
+  }
+  return p;
+}
+
+struct ModelDev {
+  float *P, *M, *V, *G, *X, *Y, *out, *work;
+};
+ModelDev model_dev(void* base) {
+  float* f = (float*)base;
+  ModelDev d;
+  d.P = f;
+  d.M = d.P + QR_MLP_NPARAMS;
+  d.V = d.M + QR_MLP_NPARAMS;
+  d.G = d.V + QR_MLP_NPARAMS;
+  d.X = d.G + QR_MLP_NPARAMS + 1;
+  d.Y = d.X + 4 * kModelCap;
+  d.out = d.Y + kModelCap;
+  d.work = d.out + kModelCap;
+  return d;
+}
+
+// Fits the model to the samples from the same initial weights every time
+// (full batch, Adam); synchronous.
+int model_fit(const std::vector<Sample>& data, const std::vector<std::pair<int, int>>& pairs, void* base,
+              cudaStream_t st, Model* md) {
+  const int ns = (int)std::min<size_t>(data.size(), kModelCap);
+  if (ns < 2) return -1;
+  std::vector<float> X(4 * (size_t)ns), Y(ns);
+  double mu[4] = {0, 0, 0, 0}, sq[4] = {0, 0, 0, 0}, ym = 0;
+  for (int s = 0; s < ns; ++s) {
+    raw_features(data[s].m, data[s].n, data[s].nb, data[s].ib, &X[4 * s]);
+    for (int i = 0; i < 4; ++i) mu[i] += X[4 * s + i];
+    ym += std::log(data[s].sec);
+  }
+  Model m;
+  for (int i = 0; i < 4; ++i) mu[i] /= ns;
+  for (int s = 0; s < ns; ++s)
+    for (int i = 0; i < 4; ++i) sq[i] += (X[4 * s + i] - mu[i]) * (X[4 * s + i] - mu[i]);
+  for (int i = 0; i < 4; ++i) {
+    m.mean[i] = (float)mu[i];
+    const double sd = std::sqrt(sq[i] / ns);
+    m.sd[i] = sd > 0 ? (float)sd : 1.f;
+  }
+  m.ymean = (float)(ym / ns);
+  for (int s = 0; s < ns; ++s) {
+    for (int i = 0; i < 4; ++i) X[4 * s + i] = (X[4 * s + i] - m.mean[i]) / m.sd[i];
+    Y[s] = (float)std::log(data[s].sec) - m.ymean;
+  }
+  m.params = model_init(0x5EED0001ull);
+  const ModelDev d = model_dev(base);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d.P, m.params.data(), sizeof(float) * QR_MLP_NPARAMS, cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemsetAsync(d.M, 0, sizeof(float) * 2 * QR_MLP_NPARAMS, st)) ||
+      (e = cudaMemcpyAsync(d.X, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(d.Y, Y.data(), sizeof(float) * ns, cudaMemcpyHostToDevice, st)))
+    return (int)e;
+  int rc = qr_mlp_train(ns, d.X, d.Y, d.P, d.M, d.V, kModelSteps, kModelLr, d.G, d.work, st);
+  if (rc) return rc;
+  if ((e = cudaMemcpyAsync(m.params.data(), d.P, sizeof(float) * QR_MLP_NPARAMS, cudaMemcpyDeviceToHost, st)))
+    return (int)e;
+  if ((e = cudaStreamSynchronize(st))) return (int)e;
+  m.pairs = pairs;
+  m.ok = true;
+  *md = m;
+  return 0;
+}
+
+// Predicted seconds of each (NB, IB) at (m, n); synchronous.
+int model_predict(const Model& md, int64_t m, int64_t n, const std::vector<std::pair<int, int>>& pairs, void* base,
+                  cudaStream_t st, std::vector<double>* sec) {
+  const int np = (int)pairs.size();
+  if (np == 0 || np > kModelCap) return -1;
+  std::vector<float> X(4 * (size_t)np), out(np);
+  for (int s = 0; s < np; ++s) {
+    raw_features(m, n, pairs[s].first, pairs[s].second, &X[4 * s]);
+    for (int i = 0; i < 4; ++i) X[4 * s + i] = (X[4 * s + i] - md.mean[i]) / md.sd[i];
+  }
+  const ModelDev d = model_dev(base);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d.P, md.params.data(), sizeof(float) * QR_MLP_NPARAMS, cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(d.X, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, st)))
+    return (int)e;
+  int rc = qr_mlp_forward(np, d.X, d.P, d.out, st);
+  if (rc) return rc;
+  if ((e = cudaMemcpyAsync(out.data(), d.out, sizeof(float) * np, cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaStreamSynchronize(st)))
+    return (int)e;
+  sec->resize(np);
+  for (int s = 0; s < np; ++s) (*sec)[s] = std::exp((double)out[s] + md.ymean);
+  return 0;
+}
+
+std::string model_json(const Model& md) {
+  std::string s = "  \"model\": {\"mean\": [";
+  char b[64];
+  for (int i = 0; i < 4; ++i) {
+    snprintf(b, sizeof(b), "%s%.9g", i ? ", " : "", md.mean[i]);
+    s += b;
+  }
+  s += "], \"sd\": [";
+  for (int i = 0; i < 4; ++i) {
+    snprintf(b, sizeof(b), "%s%.9g", i ? ", " : "", md.sd[i]);
+    s += b;
+  }
+  snprintf(b, sizeof(b), "], \"ymean\": %.9g, \"pairs\": [", md.ymean);
+  s += b;
+  for (size_t i = 0; i < md.pairs.size(); ++i) {
+    snprintf(b, sizeof(b), "%s[%d, %d]", i ? ", " : "", md.pairs[i].first, md.pairs[i].second);
+    s += b;
+  }
+  s += "], \"params\": [";
+  for (size_t i = 0; i < md.params.size(); ++i) {
+    snprintf(b, sizeof(b), "%s%.9g", i ? ", " : "", md.params[i]);
+    s += b;
+  }
+  s += "]},\n";
+  return s;
+}
+
+// Parses the "model" object written by model_json; false if absent or malformed.
+bool parse_model(const std::string& s, Model* md) {
+  size_t p = s.find("\"model\": {");
+  if (p == std::string::npos) return false;
+  Model m;
+  auto read_floats = [&](const char* key, float* out, size_t count, size_t* pos) {
+    size_t q = s.find(key, *pos);
+    if (q == std::string::npos) return false;
+    q = s.find('[', q);
+    if (q == std::string::npos) return false;
+    const char* c = s.c_str() + q + 1;
+    for (size_t i = 0; i < count; ++i) {
+      char* end = nullptr;
+      out[i] = strtof(c, &end);
+      if (end == c) return false;
+      c = end;
+      while (*c == ',' || *c == ' ' || *c == '\n') ++c;
+    }
+    *pos = (size_t)(c - s.c_str());
+    return true;
+  };
+  size_t pos = p;
+  if (!read_floats("\"mean\"", m.mean, 4, &pos) || !read_floats("\"sd\"", m.sd, 4, &pos)) return false;
+  size_t q = s.find("\"ymean\": ", pos);
+  if (q == std::string::npos) return false;
+  m.ymean = strtof(s.c_str() + q + 9, nullptr);
+  q = s.find("\"pairs\": [", q);
+  if (q == std::string::npos) return false;
+  q += 10;
+  while (true) {
+    int a, b;
+    while (q < s.size() && (s[q] == ' ' || s[q] == ',')) ++q;
+    if (q >= s.size() || s[q] != '[') break;
+    if (sscanf(s.c_str() + q, "[%d, %d]", &a, &b) != 2) return false;
+    m.pairs.push_back({a, b});
+    q = s.find(']', q) + 1;
+  }
+  m.params.resize(QR_MLP_NPARAMS);
+  pos = q;
+  if (!read_floats("\"params\"", m.params.data(), QR_MLP_NPARAMS, &pos)) return false;
+  if (m.pairs.empty()) return false;
+  m.ok = true;
+  *md = m;
+  return true;
+}
+
 // --- resumable JSONL log ------------------------------------------------------
 struct LogKey {
-  int kind;  // 1 = step 1, 2 = step 2 (p = 1), 3 = domain sweep of a tall shape
+  // 1 = step 1, 2 = step 2 (p = 1), 3 = domain sweep of a tall shape,
+  // 4 = the model's predicted seconds (not reused), 5 = step 1 (MultCallFlushLRU)
+  int kind;
   int64_t m, n;
   int nb, ib;
   int p;
@@ -382,9 +660,13 @@ int qr_load_table(const char* path) {
   if (!path) return -1;
   int prec = 0;
   std::vector<Entry> t;
-  if (!read_table(path, &prec, &t)) return -1;
+  std::string text;
+  if (!read_table(path, &prec, &t, &text)) return -1;
+  Model md;
+  const bool has_model = parse_model(text, &md);
   std::lock_guard<std::mutex> lock(g_tmu);
   g_table[prec] = t;
+  g_model[prec] = has_model ? md : Model();
   return 0;
 }
 
@@ -392,6 +674,35 @@ int qr_clear_tables(void) {
   std::lock_guard<std::mutex> lock(g_tmu);
   g_table[0].clear();
   g_table[1].clear();
+  g_model[0] = Model();
+  g_model[1] = Model();
+  return 0;
+}
+
+int qr_model_propose(int64_t m, int64_t n, int prec, int* nb, int* ib, double* seconds, void* d_work,
+                     int64_t work_bytes, void* stream) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
+  if (!nb) return -4;
+  if (!ib) return -5;
+  if (!d_work) return -7;
+  if (work_bytes < kModelBytes) return -8;
+  Model md;
+  {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    md = g_model[prec == QR_PREC_F32 ? 1 : 0];
+  }
+  if (!md.ok) return 1;  // no trained model for this precision
+  std::vector<double> sec;
+  int rc = model_predict(md, m, n, md.pairs, d_work, (cudaStream_t)stream, &sec);
+  if (rc) return rc;
+  size_t bi = 0;
+  for (size_t c = 1; c < sec.size(); ++c)
+    if (sec[c] < sec[bi]) bi = c;
+  *nb = md.pairs[bi].first;
+  *ib = md.pairs[bi].second;
+  if (seconds) *seconds = sec[bi];
   return 0;
 }
 
@@ -467,24 +778,28 @@ int64_t qr_tune_nearest(int64_t value, const int64_t* grid, int ngrid) {
   return best;
 }
 
-int qr_step1_workspace(int nb, int prec, int64_t* bytes) {
+int qr_step1_workspace(int nb, int prec, int flush, int64_t* bytes) {
   if (nb < 8 || nb > 512) return -1;
-  if (!bytes) return -3;
-  *bytes = step1_bytes(nb, 2 * sm_count(), prec == QR_PREC_F32 ? 4 : 8);
+  if (flush != 0 && flush != 1) return -3;
+  if (!bytes) return -4;
+  const size_t esz = prec == QR_PREC_F32 ? 4 : 8;
+  *bytes = flush ? step1_flush_bytes(nb, 2 * sm_count(), esz) : step1_bytes(nb, 2 * sm_count(), esz);
   return 0;
 }
 
-int qr_step1_time(int nb, int ib, int prec, int launches, double* seconds_per_launch, double* gflops,
+int qr_step1_time(int nb, int ib, int prec, int launches, int flush, double* seconds_per_launch, double* gflops,
                   void* d_work, int64_t work_bytes, void* stream) {
   if (nb < 8 || nb > 512) return -1;
   if (ib < 1 || ib > nb || ib > 256) return -2;
   if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
-  if (!seconds_per_launch) return -5;
+  if (flush != 0 && flush != 1) return -5;
+  if (!seconds_per_launch) return -6;
   const int nbatch = 2 * sm_count();
   double s = 0;  // launches <= 0: adaptive count (3..50)
-  const int rc = prec == QR_PREC_F64
-                     ? step1_time<double>(nb, ib, nbatch, launches, &s, d_work, work_bytes, (cudaStream_t)stream)
-                     : step1_time<float>(nb, ib, nbatch, launches, &s, d_work, work_bytes, (cudaStream_t)stream);
+  const int rc =
+      prec == QR_PREC_F64
+          ? step1_time<double>(nb, ib, nbatch, launches, flush, &s, d_work, work_bytes, (cudaStream_t)stream)
+          : step1_time<float>(nb, ib, nbatch, launches, flush, &s, d_work, work_bytes, (cudaStream_t)stream);
   if (rc) return rc;
   *seconds_per_launch = s;
   if (gflops) *gflops = nbatch * 4.0 * nb * (double)nb * nb / s / 1e9;
@@ -495,7 +810,7 @@ int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t* bytes) {
   if (max_m < 1 || max_n < 1 || max_n > max_m) return -1;
   if (!bytes) return -4;
   const size_t esz = prec == QR_PREC_F32 ? 4 : 8;
-  int64_t best = step1_bytes(512, 2 * sm_count(), esz);
+  int64_t best = step1_bytes(512, 2 * sm_count(), esz) + step1_flush_extra(esz);
   for (int nb = 64; nb <= 512; nb += 32) {
     int64_t t_el = 0, sb = 0;
     // the domain-tree path (tall-skinny p sweep) needs the larger scratch
@@ -504,7 +819,7 @@ int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t* bytes) {
                          (int64_t)((t_el * esz + 255) & ~(size_t)255) + sb;
     best = std::max(best, need);
   }
-  *bytes = best;
+  *bytes = best + kModelBytes;  // the cost model's buffers come first
   return 0;
 }
 
@@ -533,22 +848,34 @@ int qr_time_factor_p(int64_t m, int64_t n, int nb, int ib, int p, int prec, int 
                                                    median_s, min_s);
 }
 
-int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, int mode, int reps, int prec,
-            const char* table_path, const char* log_path, void* d_work, int64_t work_bytes, double* seconds_out,
-            void* stream) {
+int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, int mode, int use_model, int reps,
+            int prec, const char* table_path, const char* log_path, void* d_work, int64_t work_bytes,
+            double* seconds_out, void* stream) {
   if (!ms || !ns || nshapes < 1) return -1;
   if (heuristic < 0 || heuristic > 2) return -4;
-  if (mode < 0 || mode > 1) return -5;
-  if (reps < 1) return -6;
-  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -7;
-  if (!d_work) return -10;
+  if (mode < 0 || mode > 3) return -5;
+  if (use_model < 0 || use_model > 8) return -6;
+  if (reps < 1) return -7;
+  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -8;
+  if (!d_work) return -11;
+  if (work_bytes <= kModelBytes) return -12;
+  const bool exhaustive = (mode & 1) != 0;
+  const int flush = (mode >> 1) & 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  void* mwork = d_work;  // the cost model's buffers
+  void* fwork = (char*)d_work + kModelBytes;
+  const int64_t fbytes = work_bytes - kModelBytes;
   const auto t_start = std::chrono::steady_clock::now();
+  auto since = [](std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  };
   std::map<LogKey, double> seen;
   read_log(log_path, &seen);
   auto grid = grid_pairs(64, 512, 32, 8);
   std::vector<std::pair<int, int>> cand;
-  double step1_s = 0;
-  if (mode == 1) {
+  double step1_s = 0, model_s = 0;
+  const int step1_kind = flush ? 5 : 1;
+  if (exhaustive) {
     cand = grid;  // exhaustive search over the grid
   } else {
     std::vector<int> nb(grid.size()), ib(grid.size());
@@ -557,15 +884,15 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       nb[g] = grid[g].first;
       ib[g] = grid[g].second;
       double s = 0, gf = 0;
-      auto it = seen.find(LogKey{1, 0, 0, nb[g], ib[g], 1});
+      auto it = seen.find(LogKey{step1_kind, 0, 0, nb[g], ib[g], 1});
       if (it != seen.end()) {
         s = it->second;
       } else {
         const auto t0 = std::chrono::steady_clock::now();
-        int rc = qr_step1_time(nb[g], ib[g], prec, 0, &s, &gf, d_work, work_bytes, stream);
+        int rc = qr_step1_time(nb[g], ib[g], prec, 0, flush, &s, &gf, fwork, fbytes, stream);
         if (rc) return rc;
-        step1_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        append_log(log_path, 1, 0, 0, nb[g], ib[g], s, s, 0);
+        step1_s += since(t0);
+        append_log(log_path, step1_kind, 0, 0, nb[g], ib[g], s, s, 0);
       }
       perf[g] = 2.0 * sm_count() * 4.0 * nb[g] * (double)nb[g] * nb[g] / s / 1e9;
     }
@@ -580,30 +907,79 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
   std::sort(order.begin(), order.end(), [&](int a, int b) { return std::tie(ns[a], ms[a]) < std::tie(ns[b], ms[b]); });
   std::vector<Entry> table;
   std::vector<std::pair<int, int>> surv = cand;
+  std::vector<Sample> train;  // Step-2 timings of the orders done so far
   double step2_s = 0;
-  int measured = 0;
+  int measured = 0, done = 0, fallbacks = 0;
   for (int oi : order) {
     const int64_t m = ms[oi], n = ns[oi];
-    std::vector<double> perf(surv.size(), 0.0);
-    for (size_t c = 0; c < surv.size(); ++c) {
+    const size_t ns_ = surv.size();
+    std::vector<double> perf(ns_, 0.0), sec(ns_, 0.0);
+    std::vector<char> have(ns_, 0);
+    auto measure = [&](size_t c) -> int {
       double med = 0, mn = 0;
       auto it = seen.find(LogKey{2, m, n, surv[c].first, surv[c].second, 1});
       if (it != seen.end()) {
         med = it->second;
       } else {
         const auto t0 = std::chrono::steady_clock::now();
-        int rc = qr_time_factor(m, n, surv[c].first, surv[c].second, prec, reps, &med, &mn, d_work, work_bytes,
-                                stream);
+        int rc = qr_time_factor(m, n, surv[c].first, surv[c].second, prec, reps, &med, &mn, fwork, fbytes, stream);
         if (rc) return rc;
-        step2_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        step2_s += since(t0);
         append_log(log_path, 2, m, n, surv[c].first, surv[c].second, med, mn, reps);
         ++measured;
       }
+      sec[c] = med;
       perf[c] = qr_flops_d(m, n) / med / 1e9;
+      have[c] = 1;
+      train.push_back(Sample{m, n, surv[c].first, surv[c].second, med});
+      return 0;
+    };
+    // With the model (use_model = k > 0, PSPAYG, from the third order on):
+    // fit it to the timings so far, rank the survivors by predicted time and
+    // measure the k best; keep going down the ranking while the last one
+    // measured is the fastest so far, and measure every survivor when a
+    // prediction of a measured pair is off by more than the trust margin.
+    const bool guided = use_model > 0 && !exhaustive && done >= 2 && (int)ns_ > use_model && train.size() >= 4;
+    if (!guided) {
+      for (size_t c = 0; c < ns_; ++c)
+        if (int rc = measure(c)) return rc;
+    } else {
+      const auto t0 = std::chrono::steady_clock::now();
+      Model md;
+      std::vector<double> pred;
+      int rc = model_fit(train, cand, mwork, st, &md);
+      if (!rc) rc = model_predict(md, m, n, surv, mwork, st, &pred);
+      if (rc) return rc;
+      model_s += since(t0);
+      for (size_t c = 0; c < ns_; ++c)
+        append_log(log_path, 4, m, n, surv[c].first, surv[c].second, pred[c], pred[c], 0);
+      std::vector<size_t> rank(ns_);
+      for (size_t c = 0; c < ns_; ++c) rank[c] = c;
+      std::stable_sort(rank.begin(), rank.end(), [&](size_t a, size_t b) { return pred[a] < pred[b]; });
+      size_t r = 0;
+      for (; r < (size_t)use_model; ++r)
+        if (int rc2 = measure(rank[r])) return rc2;
+      auto fastest = [&]() {
+        size_t b = rank[0];
+        for (size_t q = 0; q < r; ++q)
+          if (sec[rank[q]] < sec[b]) b = rank[q];
+        return b;
+      };
+      while (r < ns_ && fastest() == rank[r - 1])
+        if (int rc2 = measure(rank[r++])) return rc2;
+      bool trusted = true;
+      for (size_t q = 0; q < r; ++q)
+        if (std::fabs(std::log(sec[rank[q]]) - std::log(pred[rank[q]])) > kModelTrust) trusted = false;
+      if (!trusted) {
+        ++fallbacks;
+        for (; r < ns_; ++r)
+          if (int rc2 = measure(rank[r])) return rc2;
+      }
     }
-    size_t bi = 0;
-    for (size_t c = 1; c < surv.size(); ++c)
-      if (perf[c] > perf[bi] || (perf[c] == perf[bi] && surv[c].first < surv[bi].first)) bi = c;
+    size_t bi = ns_;
+    for (size_t c = 0; c < ns_; ++c)
+      if (have[c] && (bi == ns_ || perf[c] > perf[bi] || (perf[c] == perf[bi] && surv[c].first < surv[bi].first)))
+        bi = c;
     Entry ent{m, n, surv[bi].first, surv[bi].second, perf[bi], 1};
     // the paper's third tunable for tall-skinny matrices: the number of
     // panel domains, swept in powers of two with the chosen (NB, IB)
@@ -616,9 +992,9 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
           med = it->second;
         } else {
           const auto t0 = std::chrono::steady_clock::now();
-          int rc = qr_time_factor_p(m, n, ent.nb, ent.ib, pd, prec, reps, &med, &mn, d_work, work_bytes, stream);
+          int rc = qr_time_factor_p(m, n, ent.nb, ent.ib, pd, prec, reps, &med, &mn, fwork, fbytes, stream);
           if (rc) return rc;
-          step2_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+          step2_s += since(t0);
           append_log(log_path, 3, m, n, ent.nb, ent.ib, med, mn, reps, pd);
           ++measured;
         }
@@ -629,34 +1005,64 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
         }
       }
     table.push_back(ent);
-    if (mode == 0 && m == n) {  // prune as you go along the square orders
-      std::vector<int> nbv(surv.size()), keep(surv.size());
-      for (size_t c = 0; c < surv.size(); ++c) nbv[c] = surv[c].first;
-      qr_tune_payg((int)surv.size(), nbv.data(), perf.data(), keep.data());
+    if (!exhaustive && m == n) {  // prune as you go along the square orders
+      // Property 5.1 among the pairs measured at this order; a survivor the
+      // model left unmeasured is kept
+      std::vector<int> nbv, keep;
+      std::vector<double> pv;
+      std::vector<size_t> idx;
+      for (size_t c = 0; c < ns_; ++c)
+        if (have[c]) {
+          nbv.push_back(surv[c].first);
+          pv.push_back(perf[c]);
+          idx.push_back(c);
+        }
+      keep.resize(nbv.size());
+      qr_tune_payg((int)nbv.size(), nbv.data(), pv.data(), keep.data());
+      std::vector<char> drop(ns_, 0);
+      for (size_t q = 0; q < idx.size(); ++q)
+        if (!keep[q]) drop[idx[q]] = 1;
       std::vector<std::pair<int, int>> nx;
-      for (size_t c = 0; c < surv.size(); ++c)
-        if (keep[c]) nx.push_back(surv[c]);
+      for (size_t c = 0; c < ns_; ++c)
+        if (!drop[c]) nx.push_back(surv[c]);
       surv = nx;
     }
+    ++done;
   }
-  const double total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  // the final model, fitted to every Step-2 timing, proposes pairs for
+  // untuned shapes (qr_model_propose) and is saved with the table
+  Model final_model;
+  if (use_model > 0 && train.size() >= 4) {
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = model_fit(train, cand, mwork, st, &final_model);
+    if (rc) return rc;
+    model_s += since(t0);
+  }
+  const double total = since(t_start);
   if (seconds_out) {
     seconds_out[0] = total;
     seconds_out[1] = step1_s;
     seconds_out[2] = step2_s;
     seconds_out[3] = (double)measured;
+    seconds_out[4] = model_s;
+    seconds_out[5] = (double)fallbacks;
   }
   {
     std::lock_guard<std::mutex> lock(g_tmu);
     g_table[prec == QR_PREC_F32 ? 1 : 0] = table;
+    g_model[prec == QR_PREC_F32 ? 1 : 0] = final_model;
   }
   if (table_path && table_path[0]) {
-    char extra[512];
+    char extra[768];
     snprintf(extra, sizeof(extra),
-             "  \"heuristic\": %d,\n  \"mode\": \"%s\",\n  \"reps\": %d,\n  \"seconds\": %.3f,\n  \"step1_seconds\": "
-             "%.3f,\n  \"step2_seconds\": %.3f,\n",
-             heuristic, mode ? "exhaustive" : "pspayg", reps, total, step1_s, step2_s);
-    if (!write_table(table_path, prec == QR_PREC_F32 ? 1 : 0, table, extra)) return -8;
+             "  \"heuristic\": %d,\n  \"mode\": \"%s\",\n  \"step1\": \"%s\",\n  \"use_model\": %d,\n"
+             "  \"reps\": %d,\n  \"seconds\": %.3f,\n  \"step1_seconds\": %.3f,\n  \"step2_seconds\": %.3f,\n"
+             "  \"model_seconds\": %.3f,\n  \"factorizations_timed\": %d,\n  \"model_fallbacks\": %d,\n",
+             heuristic, exhaustive ? "exhaustive" : "pspayg", flush ? "multcallflushlru" : "noflush", use_model,
+             reps, total, step1_s, step2_s, model_s, measured, fallbacks);
+    std::string ex = extra;
+    if (final_model.ok) ex += model_json(final_model);
+    if (!write_table(table_path, prec == QR_PREC_F32 ? 1 : 0, table, ex)) return -9;
   }
   return 0;
 }

@@ -3,7 +3,9 @@ and ticket order that bench.py times), through properties the CPU can check
 entry by entry: R^T R = A^T A on sampled entries (invariant to R's row
 signs, independent of Q), Q^T a_j = r_j on sampled columns through the
 separate Q-application kernel, and Q^T (A Z) = R Z with Q^T applied on the
-CPU from the stored reflectors and T factors (oracle/tile_apply.py)."""
+CPU from the stored reflectors and T factors (oracle/tile_apply.py); and,
+marked slow, |R| itself against the oracle's unblocked Householder R of the
+same matrix up to row signs, at 1e-10 relative."""
 import numpy as np
 import pytest
 
@@ -78,3 +80,19 @@ def test_bench_size_stored_factors_applied_on_cpu(q, fact):
     RZ = np.triu(F) @ Z
     err = np.linalg.norm(QtAZ - RZ) / (np.linalg.norm(A) * np.linalg.norm(Z))
     assert err <= 10 * N * U, err
+
+
+@pytest.mark.slow
+def test_bench_size_r_matches_oracle(q, fact):
+    """||D R_gpu - R_oracle||_F / ||R_oracle||_F <= 1e-10, D = diag(+-1) from
+    the diagonal signs: the |R| agreement criterion at the benchmark's size
+    (the oracle's dgeqr2-style QR of the same N = 10000 matrix)."""
+    import oracle
+    A, f, nb, ib = fact
+    F, _ = oracle.geqr2(A)
+    R_or = np.triu(F)
+    del F
+    R = np.triu(f.A.cpu().numpy())
+    D = oracle.row_signs(R, R_or)
+    rel = np.linalg.norm(D[:, None] * R - R_or) / np.linalg.norm(R_or)
+    assert rel <= 1e-10, rel

@@ -60,6 +60,9 @@ def test_noalloc_matches_qr_factor_d(q, m, n, nb, ib):
 def test_noalloc_rejects_oversize(q):
     L = q.lib()
     A = torch.empty(1, dtype=torch.float64, device="cuda")
-    # 4096 x 4096 needs 128 MiB of scratch, more than the fixed array
+    # 4096 x 4096 needs 128 MiB of scratch, more than the fixed array; the
+    # code (QR_NOALLOC_TOO_LARGE) differs from every argument error
     rc = L.qr_factor_d_noalloc(4096, 4096, _ptr(A), 4096, 128, 32, _ptr(A), None, None)
-    assert rc == -1
+    assert rc == -100
+    # a bad argument still reports its position
+    assert L.qr_factor_d_noalloc(-1, 4, _ptr(A), 4, 128, 32, _ptr(A), None, None) == -1
