@@ -57,6 +57,10 @@ extern "C" {
 #define QR_OPT_ORDER           7 /* flat-tree ticket order: 0 earliest start time, 1 list schedule (default) */
 #define QR_OPT_PANEL_WEIGHT    8 /* list schedule: GEQRT/TSQRT cost as a percentage of their flops (default 150) */
 #define QR_OPT_UNMQR_WEIGHT    9 /* list schedule: UNMQR cost as a percentage of its flops (default 100) */
+#define QR_OPT_LS_REFINE      10 /* qr_solve_ls refinement: 0 automatic (F32 augmented, TF32/BF16X3 GMRES-IR), 1 augmented, 2 GMRES-IR */
+#define QR_OPT_GMRES_MAX      11 /* GMRES-IR: Krylov dimension per refinement step (default 50, at most QR_GMRES_MAX_DIM) */
+#define QR_OPT_GMRES_TOL_EXP  12 /* GMRES-IR: inner relative residual target 10^-value (default 10) */
+#define QR_GMRES_MAX_DIM      64
 
 /*
  * qr_workspace -- sizes of the caller-owned buffers of qr_factor_*.
@@ -304,26 +308,38 @@ int qr_batched_status(const void *d_scratch, int *status, void *stream);
  * (n x nrhs) are FP64 device arrays; A and B are not modified.
  * prec = QR_PREC_F64: QR of an FP64 copy of A, X = R^{-1} (Q^T B)(0:n)
  *   (max_iter > 0 adds FP64 refinement as below).
- * prec = QR_PREC_F32: QR of an FP32 copy of A (FP64 kept in the panel's
- *   Householder vector / tau generation), then refinement of the augmented
- *   system [I A; A^T 0][r; x] = [b; 0] (Bjorck) with FP64 residuals
- *   f = b - r - A x, g = -A^T r and FP64 accumulation of x and r; each
- *   correction solves R^T h = g, d = Q^T f, R dx = d(0:n) - h,
- *   dr = Q [h; d(n:m)] with the FP32 factors. Stops when every column has
- *   ||dx|| <= tol ||x|| or after max_iter corrections.
+ * prec = QR_PREC_F32 / QR_PREC_TF32 / QR_PREC_BF16X3: QR of an FP32 copy of
+ *   A (FP64 kept in the panel's Householder vector / tau generation), its
+ *   UNMQR/TSMQR products on the FP32 cores (F32) or the tensor cores (TF32,
+ *   BF16X3, as qr_factor_mixed_s), then refinement of the augmented system
+ *   [I A; A^T 0][r; x] = [b; 0] (Bjorck) with FP64 residuals
+ *   f = b - r - A x, g = -A^T r and FP64 accumulation of x and r. The
+ *   correction M^-1 [f; g] through the low-precision factors solves
+ *   R^T h = g, d = Q^T f, R dx = d(0:n) - h, dr = Q [h; d(n:m)].
+ *   Scheme (QR_OPT_LS_REFINE; automatic: augmented refinement for F32,
+ *   GMRES-IR for TF32 and BF16X3): augmented refinement adds that
+ *   correction each step; GMRES-IR (Carson, Higham and Pranesh) solves
+ *   K [dr; dx] = [f; g], K the augmented matrix, each step by FP64 GMRES on
+ *   M^-1 K to a relative residual of 10^-QR_OPT_GMRES_TOL_EXP or at most
+ *   QR_OPT_GMRES_MAX iterations -- needed where kappa(A) u > 1 for the
+ *   factorization's precision (TF32: u = 2^-11, BF16X3: about 2^-17, so
+ *   kappa = 1e6 is beyond plain refinement). Stops when every column has
+ *   ||dx|| <= tol ||x|| or after max_iter steps.
  * nb, ib: tile order / inner blocking of the factorization (0 = tuned table).
  * p: panel domains of the factorization (qr_factor_p_*); 0 picks
  *   ceil(MT / NT) tile-row ranges per panel, at most 32 (1 = flat tree).
- * info[3] (may be NULL): corrections taken (max over RHS groups); 1 if
+ * info[4] (may be NULL): refinement steps taken (max over RHS groups); 1 if
  *   every column met ||dx|| <= tol ||x|| (1 also for a plain solve), 2 if
  *   the corrections stopped shrinking (no column's correction fell below
- *   half the previous one, from the third correction on: the limiting
- *   accuracy of FP64 residuals is reached), 0 if max_iter ran out first;
- *   device status bits (QR_DEV_*: of the factorization, and QR_DEV_TIMEOUT
- *   from the triangular solves, whose row blocks wait on each other with
- *   the same bounded waits as the scheduler).
+ *   half the previous one, from the third step on: the limiting accuracy of
+ *   FP64 residuals is reached), 0 if max_iter ran out first; device status
+ *   bits (QR_DEV_*: of the factorization, and QR_DEV_TIMEOUT from the
+ *   triangular solves, whose row blocks wait on each other with the same
+ *   bounded waits as the scheduler); GMRES iterations in total (0 for
+ *   augmented refinement).
  * d_work (>= qr_solve_ls_workspace bytes) is caller-owned. Synchronises
- * `stream` once per correction (stopping test) and at the end.
+ * `stream` once per refinement step (stopping test), once per GMRES
+ * iteration, and at the end.
  */
 int qr_solve_ls_workspace(int64_t m, int64_t n, int64_t nrhs, int prec, int nb, int ib, int p, int64_t *bytes);
 int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t lda, const double *d_B, int64_t ldb,

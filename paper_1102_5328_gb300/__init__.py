@@ -33,6 +33,9 @@ QR_OPT_RECORD_EVENTS = 6
 QR_OPT_ORDER = 7
 QR_OPT_PANEL_WEIGHT = 8
 QR_OPT_UNMQR_WEIGHT = 9
+QR_OPT_LS_REFINE = 10
+QR_OPT_GMRES_MAX = 11
+QR_OPT_GMRES_TOL_EXP = 12
 
 
 _TUNED_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")
@@ -165,6 +168,32 @@ def qr_factor(A, nb=0, ib=0, T=None, scratch=None, stream=None, p=None):
     return Factorization(A, T, scratch, nb, ib)
 
 
+def qr_factor_mixed(A, prec, nb=0, ib=0, p=None, T=None, scratch=None, stream=None):
+    """FP32 tile QR of A (float32, in place) with the UNMQR/TSMQR products at
+    precision ``prec`` (QR_PREC_F32, QR_PREC_TF32 or QR_PREC_BF16X3) through
+    qr_factor_mixed_s; p panel domains (None: the tuned table's, else 1)."""
+    m, n = A.shape
+    if A.dtype != torch.float32 or not A.is_cuda or A.stride(0) != 1:
+        raise ValueError("A must be a column-major float32 CUDA tensor")
+    lda = A.stride(1) if n > 1 else m
+    if nb == 0:
+        nb, ib, pt = qr_lookup_p(m, n, torch.float32)
+        if p is None:
+            p = pt
+    if p is None:
+        p = 1
+    t_elems, sbytes = qr_workspace_p(m, n, nb, ib, p, torch.float32) if p > 1 else \
+        qr_workspace(m, n, nb, ib, torch.float32)
+    if T is None or T.numel() < t_elems:
+        T = torch.empty(max(t_elems, 1), dtype=torch.float32, device=A.device)
+    if scratch is None or scratch.numel() < sbytes:
+        scratch = torch.empty(sbytes, dtype=torch.uint8, device=A.device)
+    _lib.check(lib().qr_factor_mixed_s(m, n, ctypes.c_void_p(A.data_ptr()), lda, nb, ib, p, prec,
+                                       ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(scratch.data_ptr()), sbytes,
+                                       _stream_ptr(stream)), "qr_factor_mixed_s")
+    return Factorization(A, T, scratch, nb, ib, p)
+
+
 def qr_apply_qt(fact, C, trans=True, stream=None, parallel=True):
     """C <- Q^T C (trans) or Q C, in place, with the factors of qr_factor.
     parallel=True uses the dependency-ordered persistent kernel
@@ -214,8 +243,9 @@ def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, 
     """min ||A X - B|| (A, B FP64, column-major CUDA tensors; unchanged).
     ``nb = 0`` takes (nb, ib) from the tuned table of the factorization's
     precision, and p too when ``p = 0`` (the C library's p = 0 picks
-    ceil(MT/NT) domains). Returns (X, info) with info = (corrections,
-    converged, device status)."""
+    ceil(MT/NT) domains). prec: QR_PREC_F64, F32, TF32 or BF16X3. Returns
+    (X, info) with info = (corrections, converged, device status, GMRES
+    iterations)."""
     m, n = A.shape
     nrhs = B.shape[1]
     if A.dtype != torch.float64 or B.dtype != torch.float64:
@@ -223,14 +253,14 @@ def qr_solve_ls(A, B, prec=QR_PREC_F64, nb=0, ib=0, max_iter=0, tol=2.0 ** -52, 
     if A.stride(0) != 1 or B.stride(0) != 1:
         raise ValueError("A and B must be column-major")
     if nb == 0:
-        nb, ib, tp = qr_lookup_p(m, n, torch.float32 if prec == QR_PREC_F32 else torch.float64)
+        nb, ib, tp = qr_lookup_p(m, n, torch.float64 if prec == QR_PREC_F64 else torch.float32)
         p = p if p else tp
     wb = ctypes.c_int64()
     _lib.check(lib().qr_solve_ls_workspace(m, n, nrhs, prec, nb, ib, p, ctypes.byref(wb)), "qr_solve_ls_workspace")
     if work is None or work.numel() < wb.value:
         work = torch.empty(wb.value, dtype=torch.uint8, device=A.device)
     X = colmajor_empty(n, nrhs, torch.float64, A.device)
-    info = (ctypes.c_int * 3)()
+    info = (ctypes.c_int * 4)()
     lda = A.stride(1) if n > 1 else m
     ldb = B.stride(1) if nrhs > 1 else m
     ldx = X.stride(1) if nrhs > 1 else n

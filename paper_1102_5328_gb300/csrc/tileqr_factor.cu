@@ -51,6 +51,9 @@ std::map<std::tuple<int, int, int>, std::array<double, 4>> g_costs;
 int g_grid_limit = 0;
 int64_t g_drop_task = -1;
 int g_record = 0;
+int g_ls_refine = 0;     // QR_OPT_LS_REFINE
+int g_gmres_max = 50;    // QR_OPT_GMRES_MAX
+int g_gmres_tol_exp = 10;  // QR_OPT_GMRES_TOL_EXP
 cudaEvent_t g_ev[2] = {nullptr, nullptr};
 bool g_ev_pending = false;
 
@@ -660,15 +663,12 @@ int qr_factor_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, flo
   return factor_impl<float>(m, n, A, lda, nb, ib, T, scratch, scratch_bytes, stream);
 }
 
+static_assert(TC_NONE == 0 && TC_TF32 == 1 && TC_BF16X3 == 2, "tc_of_prec maps onto the TC_* values");
+
 int qr_factor_mixed_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, int p, int prec, float* T,
                       void* scratch, int64_t scratch_bytes, void* stream) {
-  int tc;
-  switch (prec) {
-    case QR_PREC_F32: tc = TC_NONE; break;
-    case QR_PREC_TF32: tc = TC_TF32; break;
-    case QR_PREC_BF16X3: tc = TC_BF16X3; break;
-    default: return -8;
-  }
+  if (prec != QR_PREC_F32 && prec != QR_PREC_TF32 && prec != QR_PREC_BF16X3) return -8;
+  const int tc = tc_of_prec(prec);
   if (p < 1 || p > 4096) return -7;
   if (p == 1) return factor_impl<float>(m, n, A, lda, nb, ib, T, scratch, scratch_bytes, stream, tc);
   return qr_factor_p_tc_s(m, n, A, lda, nb, ib, p, T, scratch, scratch_bytes, stream, tc);
@@ -759,6 +759,18 @@ int qr_set_option(int opt, int64_t value) {
       if (value < 10 || value > 10000) return -2;
       g_wunmqr = (int)value;
       return 0;
+    case QR_OPT_LS_REFINE:
+      if (value < 0 || value > 2) return -2;
+      g_ls_refine = (int)value;
+      return 0;
+    case QR_OPT_GMRES_MAX:
+      if (value < 1 || value > QR_GMRES_MAX_DIM) return -2;
+      g_gmres_max = (int)value;
+      return 0;
+    case QR_OPT_GMRES_TOL_EXP:
+      if (value < 1 || value > 16) return -2;
+      g_gmres_tol_exp = (int)value;
+      return 0;
   }
   return -1;
 }
@@ -775,6 +787,9 @@ int64_t qr_get_option(int opt) {
     case QR_OPT_ORDER: return g_order;
     case QR_OPT_PANEL_WEIGHT: return g_wpanel;
     case QR_OPT_UNMQR_WEIGHT: return g_wunmqr;
+    case QR_OPT_LS_REFINE: return g_ls_refine;
+    case QR_OPT_GMRES_MAX: return g_gmres_max;
+    case QR_OPT_GMRES_TOL_EXP: return g_gmres_tol_exp;
   }
   return INT64_MIN;
 }

@@ -46,5 +46,6 @@ std::array<double, 4> qr_task_weights(int prec, int nb, int ib, int S);
 // qr_factor_p_s with the UNMQR/TSMQR products at tensor-core precision tc
 // (TC_NONE, TC_TF32, TC_BF16X3 of tc_update.cuh); the same argument checks
 // and return codes as qr_factor_p_s.
+inline int tc_of_prec(int prec) { return prec == QR_PREC_TF32 ? 1 : (prec == QR_PREC_BF16X3 ? 2 : 0); }
 int qr_factor_p_tc_s(int64_t m, int64_t n, float* A, int64_t lda, int nb, int ib, int p, float* T, void* scratch,
                      int64_t scratch_bytes, void* stream, int tc);

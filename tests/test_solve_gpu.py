@@ -154,3 +154,58 @@ def test_least_squares_full_size(q):
     assert np.all(emx <= 2 * e64), (emx, e64)
     bound = perturbation_bound(A, B, Xref, kappa)
     assert np.all(bound < 1e-8) and np.all(e64 <= bound), (e64, bound)
+
+
+@pytest.fixture
+def refine_option(q):
+    yield lambda v: q.qr_set_option(q.QR_OPT_LS_REFINE, v)
+    q.qr_set_option(q.QR_OPT_LS_REFINE, 0)
+
+
+@pytest.mark.parametrize("prec,kappa,refine", [(3, 1e6, 0), (3, 1e4, 0), (2, 1e3, 0), (1, 1e6, 2)])
+def test_gmres_ir_reaches_fp64_forward_error(q, refine_option, prec, kappa, refine):
+    """GMRES-based refinement (FP64 GMRES on the augmented system,
+    preconditioned by the low-precision QR): with BF16x3 tensor-core factors
+    (u about 2^-17, kappa u up to 15 here), TF32 factors at kappa = 1e3 and,
+    forced by QR_OPT_LS_REFINE = 2, FP32 factors, the solution reaches the
+    FP64 solve's forward error (within 2x, per RHS). Large residuals (b ~
+    N(0,1)), ragged sizes."""
+    refine_option(refine)
+    m, n = 1100, 450
+    A, B = inputs.ls_problem(m, n, 3, kappa=kappa, seed=prec * 11 + int(np.log10(kappa)))
+    Xref, _ = oracle.ls_refine(A, B, maxit=30)
+    X64, _ = q.qr_solve_ls(to_dev(A), to_dev(B), prec=q.QR_PREC_F64, nb=64, ib=16)
+    X, info = q.qr_solve_ls(to_dev(A), to_dev(B), prec=prec, nb=64, ib=16, max_iter=20, tol=1e-11)
+    e64 = fwd_err(X64.cpu().numpy(), Xref)
+    ex = fwd_err(X.cpu().numpy(), Xref)
+    assert info[2] == 0 and info[1] in (1, 2) and info[3] > 0, info
+    assert np.all(ex <= 2 * e64), (ex, e64, info)
+
+
+def test_bf16x3_plain_refinement_does_not_converge_at_kappa_1e6(q, refine_option):
+    """The reason GMRES-IR exists: with kappa u about 15 (BF16x3 factors,
+    kappa = 1e6) Bjorck's augmented refinement, forced by QR_OPT_LS_REFINE
+    = 1, stalls far from the FP64-level solution."""
+    refine_option(1)
+    m, n = 1100, 450
+    A, B = inputs.ls_problem(m, n, 2, kappa=1e6, seed=77)
+    Xref, _ = oracle.ls_refine(A, B, maxit=30)
+    X, info = q.qr_solve_ls(to_dev(A), to_dev(B), prec=q.QR_PREC_BF16X3, nb=64, ib=16, max_iter=20, tol=1e-11)
+    ex = fwd_err(X.cpu().numpy(), Xref)
+    assert info[3] == 0 and np.all(ex > 1e-6), (ex, info)
+
+
+@pytest.mark.slow
+def test_least_squares_full_size_bf16x3_gmres(q):
+    """The full-size least-squares workload with BF16x3 tensor-core factors
+    and GMRES-IR: FP64-level forward error (within 2x of the FP64 solve)."""
+    m, n, k, kappa = 16384, 4096, 8, 1e6
+    A, B = inputs.ls_problem(m, n, k, kappa=kappa, seed=5)
+    Xref, _ = oracle.ls_refine(A, B, maxit=30)
+    Ad, Bd = to_dev(A), to_dev(B)
+    X64, _ = q.qr_solve_ls(Ad, Bd, prec=q.QR_PREC_F64)
+    X, info = q.qr_solve_ls(Ad, Bd, prec=q.QR_PREC_BF16X3, max_iter=20, tol=1e-11)
+    e64 = fwd_err(X64.cpu().numpy(), Xref)
+    ex = fwd_err(X.cpu().numpy(), Xref)
+    assert info[2] == 0 and info[3] > 0, info
+    assert np.all(ex <= 2 * e64), (ex, e64, info)
