@@ -320,4 +320,253 @@ __device__ bool apply_qt_mma(const float* __restrict__ V, int ldv, const float* 
   return true;
 }
 
+// Bytes of dynamic shared memory a persistent kernel gets when its tasks
+// may take the staged tensor-core path: 96 KB, two CTAs per SM.
+constexpr int TC_SMEM_BYTES = 96 * 1024;
+
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+  unsigned r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
+// The same update with everything the inner blocks read staged once per
+// task: all nref reflectors (with the GE masks), their T factors, and per
+// chunk the top tile's rows 0..nref-1 (TS), which are updated in shared
+// memory and written back once. An inner block then costs two barriers:
+//   product 1 (partial Y^T per warp) | W = T_l^T (sum of partials + top
+//   rows), top rows -= W, one thread per column | product 2.
+// Returns false when the staged buffers do not fit the dynamic shared
+// memory of the launch (the caller then tries apply_qt_mma).
+template <int MODE, bool TS>
+__device__ bool apply_qt_mma_staged(const float* __restrict__ V, int ldv, const float* __restrict__ T, int ldt,
+                                    int nref, int IB, float* Ctop, int ldct, float* C, int ldc, int rows, int c0,
+                                    int c1, float* smem) {
+  constexpr int KQ = MODE == TC_TF32 ? 8 : 16;
+  if (rows <= 0 || c1 <= c0 || nref <= 0) return true;
+  if (rows > 512 || IB > 32 || (ldv & 3) || (reinterpret_cast<uintptr_t>(V) & 15)) return false;
+  const TcLayout L = tc_layout(rows, c1 - c0, IB, KQ);
+  const int nrefP = (nref + IB - 1) / IB * IB + (L.IBP - IB);  // the last block reads IBP rows from l0
+  const int ldcs = L.cw + 1;                                    // top rows: one column per thread
+  const size_t nv = (size_t)nrefP * L.ldvs, nt = (size_t)IB * nref, nc = TS ? (size_t)nref * ldcs : 0;
+  // partial Y^T always go to part, never to wbuf: a warp may start the next
+  // block's product 1 while another still reads W from wbuf in product 2
+  const size_t np = (size_t)L.WR * L.IBP * L.cw, nw = (size_t)L.IBP * L.ldw;
+  if (L.RW > 64 || (nv + nt + nc + np + nw) * sizeof(float) > dyn_smem_bytes()) return false;
+  float* vbuf = smem;
+  float* tsb = vbuf + nv;
+  float* ctop = tsb + nt;
+  float* part = ctop + nc;
+  float* wbuf = part + np;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+  const int wm = warp % L.WM, wr = warp / L.WM;
+  const int rw0 = wr * L.RW;
+  const int NJ = L.RW / 8;
+  // reflectors: float4 loads down each column (rows < `rows` only; the tile
+  // column holds NB >= rows rounded up to 4 elements), masks applied in
+  // registers, zero padding to nrefP x rowsPad
+  {
+    const int q4 = L.rowsPad / 4;
+    for (int idx = tid; idx < nrefP * q4; idx += NTHREADS) {
+      const int p = idx / q4, r = 4 * (idx - p * q4);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < nref && r < rows) {
+        v = __ldcg(reinterpret_cast<const float4*>(V + r + (size_t)p * ldv));
+        float* e = &v.x;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int rr = r + u;
+          if (rr >= rows) e[u] = 0.f;
+          else if (!TS) e[u] = rr < p ? 0.f : (rr == p ? 1.f : e[u]);
+        }
+      }
+      *reinterpret_cast<float2*>(vbuf + (size_t)p * L.ldvs + r) = make_float2(v.x, v.y);
+      *reinterpret_cast<float2*>(vbuf + (size_t)p * L.ldvs + r + 2) = make_float2(v.z, v.w);
+    }
+    for (int idx = tid; idx < IB * nref; idx += NTHREADS) {
+      const int p = idx / IB, q = idx - p * IB;
+      tsb[idx] = ldg(T + q + (size_t)p * ldt);
+    }
+  }
+  for (int cs = c0; cs < c1; cs += L.cw) {
+    const int cwn = min(L.cw, c1 - cs);
+    const int colA = wm * 16 + g, colB = colA + 8;
+    const bool okA = colA < cwn, okB = colB < cwn;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = rw0 + 8 * j + 2 * t;
+      const bool in = j < NJ;
+      acc[j][0] = (in && okA && r < rows) ? ldg(C + r + (size_t)(cs + colA) * ldc) : 0.f;
+      acc[j][1] = (in && okA && r + 1 < rows) ? ldg(C + r + 1 + (size_t)(cs + colA) * ldc) : 0.f;
+      acc[j][2] = (in && okB && r < rows) ? ldg(C + r + (size_t)(cs + colB) * ldc) : 0.f;
+      acc[j][3] = (in && okB && r + 1 < rows) ? ldg(C + r + 1 + (size_t)(cs + colB) * ldc) : 0.f;
+    }
+    if (TS)
+      for (int idx = tid; idx < nref * L.cw; idx += NTHREADS) {
+        const int p = idx / L.cw, col = idx - p * L.cw;
+        ctop[p * ldcs + col] = col < cwn ? ldg(Ctop + p + (size_t)(cs + col) * ldct) : 0.f;
+      }
+    __syncthreads();  // staged reflectors, T and top rows visible
+    for (int l0 = 0; l0 < nref; l0 += IB) {
+      const int ib = min(IB, nref - l0);
+      const float* vb = vbuf + (size_t)l0 * L.ldvs;
+      // --- product 1: partial Y^T of this warp's rows
+      float y[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) y[q][0] = y[q][1] = y[q][2] = y[q][3] = 0.f;
+      if (MODE == TC_TF32) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < NJ) {
+            const uint32_t a[4] = {tf32_of(acc[j][0]), tf32_of(acc[j][2]), tf32_of(acc[j][1]), tf32_of(acc[j][3])};
+            const int rb = rw0 + 8 * j + 2 * t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (q * 8 < L.IBP) {
+                const float2 bv = *reinterpret_cast<const float2*>(vb + (q * 8 + g) * L.ldvs + rb);
+                const uint32_t b[2] = {tf32_of(bv.x), tf32_of(bv.y)};
+                mma_tf32(y[q], a, b);
+              }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          if (2 * jj < NJ) {
+            uint32_t ah[4], al[4];
+            split_bf16(acc[2 * jj][0], acc[2 * jj][1], ah[0], al[0]);
+            split_bf16(acc[2 * jj][2], acc[2 * jj][3], ah[1], al[1]);
+            split_bf16(acc[2 * jj + 1][0], acc[2 * jj + 1][1], ah[2], al[2]);
+            split_bf16(acc[2 * jj + 1][2], acc[2 * jj + 1][3], ah[3], al[3]);
+            const int rb = rw0 + 16 * jj + 2 * t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (q * 8 < L.IBP) {
+                const float* vp = vb + (q * 8 + g) * L.ldvs + rb;
+                const float2 b0 = *reinterpret_cast<const float2*>(vp);
+                const float2 b1 = *reinterpret_cast<const float2*>(vp + 8);
+                uint32_t bh[2], bl[2];
+                split_bf16(b0.x, b0.y, bh[0], bl[0]);
+                split_bf16(b1.x, b1.y, bh[1], bl[1]);
+                const uint32_t ah_[4] = {ah[0], ah[1], ah[2], ah[3]}, al_[4] = {al[0], al[1], al[2], al[3]};
+                const uint32_t bh_[2] = {bh[0], bh[1]}, bl_[2] = {bl[0], bl[1]};
+                mma_bf16(y[q], ah_, bh_);
+                mma_bf16(y[q], ah_, bl_);
+                mma_bf16(y[q], al_, bh_);
+              }
+          }
+        }
+      }
+      {
+        float* dst = part + (size_t)wr * L.IBP * L.cw;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q * 8 < L.IBP) {
+            const int p0 = q * 8 + 2 * t;
+            dst[p0 * L.cw + colA] = y[q][0];
+            dst[(p0 + 1) * L.cw + colA] = y[q][1];
+            dst[p0 * L.cw + colB] = y[q][2];
+            dst[(p0 + 1) * L.cw + colB] = y[q][3];
+          }
+      }
+      __syncthreads();
+      // --- W = T_l^T (Y + top rows), top rows -= W: one thread per column
+      if (tid < L.cw) {
+        const int col = tid;
+        float yv[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          float sum = 0.f;
+          if (q < ib) {
+            for (int w2 = 0; w2 < L.WR; ++w2) sum += part[((size_t)w2 * L.IBP + q) * L.cw + col];
+            if (TS) sum += ctop[(l0 + q) * ldcs + col];
+          }
+          yv[q] = sum;
+        }
+        const float* tb = tsb + (size_t)l0 * IB;  // T(q, p) of this block at tb[q + p * IB]
+#pragma unroll
+        for (int pp = 31; pp >= 0; --pp) {
+          // descending p, so yv[p] still holds Y(p) when W(p) is formed
+          if (pp < ib) {
+            float wv = 0.f;
+#pragma unroll
+            for (int q = 0; q <= pp; ++q) wv = fmaf(tb[q + pp * IB], yv[q], wv);
+            if (TS) ctop[(l0 + pp) * ldcs + col] -= wv;
+            wbuf[pp * L.ldw + col] = wv;
+          }
+        }
+#pragma unroll
+        for (int pp = 0; pp < 32; ++pp)
+          if (pp >= ib && pp < L.IBP) wbuf[pp * L.ldw + col] = 0.f;
+      }
+      __syncthreads();
+      // --- product 2: C^T -= W^T V_l^T
+      if (MODE == TC_TF32) {
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          if (ks * 8 < L.IBP) {
+            const int k0 = ks * 8;
+            const uint32_t a[4] = {tf32_of(-wbuf[(k0 + t) * L.ldw + colA]), tf32_of(-wbuf[(k0 + t) * L.ldw + colB]),
+                                   tf32_of(-wbuf[(k0 + t + 4) * L.ldw + colA]),
+                                   tf32_of(-wbuf[(k0 + t + 4) * L.ldw + colB])};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (j < NJ) {
+                const int n0 = rw0 + 8 * j + g;
+                const uint32_t b[2] = {tf32_of(vb[(k0 + t) * L.ldvs + n0]), tf32_of(vb[(k0 + t + 4) * L.ldvs + n0])};
+                mma_tf32(acc[j], a, b);
+              }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          if (ks * 16 < L.IBP) {
+            const int k0 = ks * 16;
+            uint32_t ah[4], al[4];
+            const float* w0 = wbuf + (k0 + 2 * t) * L.ldw;
+            split_bf16(-w0[colA], -w0[L.ldw + colA], ah[0], al[0]);
+            split_bf16(-w0[colB], -w0[L.ldw + colB], ah[1], al[1]);
+            split_bf16(-w0[8 * L.ldw + colA], -w0[9 * L.ldw + colA], ah[2], al[2]);
+            split_bf16(-w0[8 * L.ldw + colB], -w0[9 * L.ldw + colB], ah[3], al[3]);
+            const uint32_t ah_[4] = {ah[0], ah[1], ah[2], ah[3]}, al_[4] = {al[0], al[1], al[2], al[3]};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (j < NJ) {
+                const float* vp = vb + (k0 + 2 * t) * L.ldvs + rw0 + 8 * j + g;
+                uint32_t bh[2], bl[2];
+                split_bf16(vp[0], vp[L.ldvs], bh[0], bl[0]);
+                split_bf16(vp[8 * L.ldvs], vp[9 * L.ldvs], bh[1], bl[1]);
+                const uint32_t bh_[2] = {bh[0], bh[1]}, bl_[2] = {bl[0], bl[1]};
+                mma_bf16(acc[j], ah_, bh_);
+                mma_bf16(acc[j], ah_, bl_);
+                mma_bf16(acc[j], al_, bh_);
+              }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = rw0 + 8 * j + 2 * t;
+      if (j < NJ) {
+        if (okA && r < rows) stg(C + r + (size_t)(cs + colA) * ldc, acc[j][0]);
+        if (okA && r + 1 < rows) stg(C + r + 1 + (size_t)(cs + colA) * ldc, acc[j][1]);
+        if (okB && r < rows) stg(C + r + (size_t)(cs + colB) * ldc, acc[j][2]);
+        if (okB && r + 1 < rows) stg(C + r + 1 + (size_t)(cs + colB) * ldc, acc[j][3]);
+      }
+    }
+    __syncthreads();  // every product 2 has read wbuf / vb; the top rows are final
+    if (TS)
+      for (int idx = tid; idx < nref * L.cw; idx += NTHREADS) {
+        const int p = idx / L.cw, col = idx - p * L.cw;
+        if (col < cwn) stg(Ctop + p + (size_t)(cs + col) * ldct, ctop[p * ldcs + col]);
+      }
+  }
+  __syncthreads();
+  return true;
+}
+
 }  // namespace tqr

@@ -874,11 +874,13 @@ template <typename S>
 __device__ void unmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C, int ldc, int c0,
                       int c1, const Smem<S>& sm, int tc = TC_NONE) {
   if constexpr (sizeof(S) == 4) {
-    if (tc == TC_TF32 && apply_qt_mma<TC_TF32, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0, c1,
-                                                      sm.vs))
+    if (tc == TC_TF32 &&
+        (apply_qt_mma_staged<TC_TF32, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm.vs) ||
+         apply_qt_mma<TC_TF32, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm.vs)))
       return;
-    if (tc == TC_BF16X3 && apply_qt_mma<TC_BF16X3, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0,
-                                                          c1, sm.vs))
+    if (tc == TC_BF16X3 &&
+        (apply_qt_mma_staged<TC_BF16X3, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm.vs) ||
+         apply_qt_mma<TC_BF16X3, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm.vs)))
       return;
   }
   apply_qt<S, false>(V, ldv, T, IB, false, 0, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm);
@@ -894,10 +896,12 @@ __device__ void tsmqr(const S* V, int ldv, const S* T, int IB, int rows, int nre
                       int ldc2, int c0, int c1, const Smem<S>& sm, bool tri = false, int tc = TC_NONE) {
   if constexpr (sizeof(S) == 4) {
     if (!tri && tc == TC_TF32 &&
-        apply_qt_mma<TC_TF32, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs))
+        (apply_qt_mma_staged<TC_TF32, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs) ||
+         apply_qt_mma<TC_TF32, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs)))
       return;
     if (!tri && tc == TC_BF16X3 &&
-        apply_qt_mma<TC_BF16X3, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs))
+        (apply_qt_mma_staged<TC_BF16X3, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs) ||
+         apply_qt_mma<TC_BF16X3, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs)))
       return;
   }
   apply_qt<S, true>(V, ldv, T, IB, false, 0, nref, IB, C1, ldc1, C2, ldc2, tri ? min(rows, nref) : rows, c0, c1,

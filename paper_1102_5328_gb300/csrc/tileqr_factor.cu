@@ -367,13 +367,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) persistent_qr(FactorArgs<S> a) {
 }
 
 template <typename S>
-int persistent_grid(int* grid_out) {
+int persistent_grid(int* grid_out, size_t smem) {
   int dev = 0, sms = 0, occ = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return (int)e;
-  const size_t smem = smem_elems<S>() * sizeof(S);
   e = cudaFuncSetAttribute(persistent_qr<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_qr<S>, NTHREADS, smem);
@@ -432,8 +431,11 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
   const int64_t nzero = (int64_t)(L.off_cnt / sizeof(unsigned)) + (int64_t)L.MT * L.NT * L.S;
   cm_to_tiles<S><<<1184, 256, 0, st>>>(A, lda, m, n, W, nb, L.MT, L.NT, (unsigned*)base, nzero);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
+  // the staged tensor-core updates take more shared memory (two CTAs per SM still fit)
+  const size_t smem = (sizeof(S) == 4 && tc != TC_NONE) ? std::max<size_t>(smem_elems<S>() * sizeof(S), TC_SMEM_BYTES)
+                                                       : smem_elems<S>() * sizeof(S);
   int grid = 0;
-  int rc = persistent_grid<S>(&grid);
+  int rc = persistent_grid<S>(&grid, smem);
   if (rc) return rc;
   FactorArgs<S> fa;
   fa.W = W; fa.T = T; fa.m = m; fa.n = n; fa.NB = nb; fa.IB = ib; fa.MT = L.MT; fa.NT = L.NT; fa.S_ = L.S;
@@ -448,7 +450,7 @@ int factor_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, S* T, v
     }
     cudaEventRecord(g_ev[0], st);
   }
-  persistent_qr<S><<<grid, NTHREADS, smem_elems<S>() * sizeof(S), st>>>(fa);
+  persistent_qr<S><<<grid, NTHREADS, smem, st>>>(fa);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   if (g_record) {
     cudaEventRecord(g_ev[1], st);
@@ -586,7 +588,7 @@ int factor_noalloc_impl(int64_t m, int64_t n, double* A, int64_t lda, int nb, in
   cm_to_tiles<double><<<1184, 256, 0, st>>>(A, lda, m, n, W, nb, L.MT, L.NT, (unsigned*)base, nzero);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   int grid = 0;
-  int rc = persistent_grid<double>(&grid);
+  int rc = persistent_grid<double>(&grid, smem_elems<double>() * sizeof(double));
   if (rc) return rc;
   FactorArgs<double> fa;
   fa.W = W; fa.T = T; fa.m = m; fa.n = n; fa.NB = nb; fa.IB = ib; fa.MT = L.MT; fa.NT = L.NT; fa.S_ = L.S;

@@ -513,7 +513,9 @@ int factor_p_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, int p
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = smem_elems<S>() * sizeof(S);
+  // the staged tensor-core updates take more shared memory (two CTAs per SM still fit)
+  const size_t smem = (sizeof(S) == 4 && tc != TC_NONE) ? std::max<size_t>(smem_elems<S>() * sizeof(S), TC_SMEM_BYTES)
+                                                       : smem_elems<S>() * sizeof(S);
   e = cudaFuncSetAttribute(persistent_qr_dag<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persistent_qr_dag<S>, NTHREADS, smem);
