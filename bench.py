@@ -263,8 +263,10 @@ def run_batched(args):
 
 def run_ls(args):
     """Least squares, A = U diag(sigma) V^T (16384 x 4096, kappa 1e6), 8 RHS:
-    plain FP64 QR solve vs FP32 factorization + FP64 augmented refinement;
-    forward error against the oracle's doubled-precision refined solution."""
+    plain FP64 QR solve vs FP32 factorization + FP64 augmented refinement vs
+    tensor-core (BF16x3, TF32) factorizations + FP64 GMRES-based refinement;
+    forward error against the oracle's doubled-precision refined solution.
+    Also the factorization alone at each low precision (CUDA events)."""
     import torch
 
     import paper_1102_5328_gb300 as q
@@ -275,14 +277,20 @@ def run_ls(args):
     A_np, B_np = inputs.ls_problem(m, n, k, kappa=1e6, seed=5)
     A = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()
     B = torch.from_numpy(np.ascontiguousarray(B_np.T)).cuda().t()
+    names = {"fp64": ("fp64", q.QR_PREC_F64, 0, 0), "fp32": ("mixed_fp32_ir", q.QR_PREC_F32, 50, 1),
+             "fp32_gmres": ("mixed_fp32_gmres_ir", q.QR_PREC_F32, 50, 2),
+             "bf16x3": ("mixed_bf16x3_gmres_ir", q.QR_PREC_BF16X3, 20, 2),
+             "tf32": ("mixed_tf32_gmres_ir", q.QR_PREC_TF32, 20, 2)}
     res = {}
-    for name, prec, it in (("fp64", q.QR_PREC_F64, 0), ("mixed_fp32_ir", q.QR_PREC_F32, 50)):
-        dt = torch.float32 if prec == q.QR_PREC_F32 else torch.float64
+    for key in args.ls_precs.split(","):
+        name, prec, it, refine = names[key]
+        q.qr_set_option(q.QR_OPT_LS_REFINE, refine)
+        dt = torch.float64 if prec == q.QR_PREC_F64 else torch.float32
         nb, ib, pd = q.qr_lookup_p(m, n, dt)
         if args.nb:
             nb, ib = args.nb, args.ib
         pd = args.ls_p if args.ls_p else pd
-        tol = args.ls_tol if prec == q.QR_PREC_F32 else 2.0 ** -52
+        tol = args.ls_tol if prec != q.QR_PREC_F64 else 2.0 ** -52
         X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it, tol=tol, p=pd)  # warm-up
         torch.cuda.synchronize()
         ts = []
@@ -292,7 +300,27 @@ def run_ls(args):
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         res[name] = {"median_s": statistics.median(ts), "info": list(info), "nb": nb, "ib": ib, "p": pd, "tol": tol,
+                     "refine": ["none", "augmented", "gmres"][refine] if prec != q.QR_PREC_F64 else "none",
                      "X": X.cpu().numpy()}
+    q.qr_set_option(q.QR_OPT_LS_REFINE, 0)
+    # the FP32-storage factorization alone, FP32 cores vs tensor cores
+    fac = {}
+    nb, ib, pd = q.qr_lookup_p(m, n, torch.float32)
+    A32 = torch.from_numpy(np.ascontiguousarray(A_np.T.astype(np.float32))).cuda().t()
+    for pname, prec in (("fp32", q.QR_PREC_F32), ("tf32", q.QR_PREC_TF32), ("bf16x3", q.QR_PREC_BF16X3)):
+        W = A32.clone()
+        f = q.qr_factor_mixed(W, prec, nb, ib, pd)
+        ms = []
+        for _ in range(max(args.steps, 3)):
+            W.copy_(A32)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            q.qr_factor_mixed(W, prec, nb, ib, pd, T=f.T, scratch=f.scratch)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        fac[pname] = {"median_ms": statistics.median(ms), "gflops": q.qr_flops(m, n) / statistics.median(ms) / 1e6,
+                      "nb": nb, "ib": ib, "p": pd, "status": f.status()}
     line = {"workload": "least squares %dx%d, kappa 1e6, %d RHS N(0,1)" % (m, n, k), "metric": "seconds per solve"}
     if not args.no_cpu:
         import oracle
@@ -312,7 +340,9 @@ def run_ls(args):
         for name in res:
             res[name].pop("X")
     line["results"] = res
-    line["speedup_mixed_over_fp64"] = res["fp64"]["median_s"] / res["mixed_fp32_ir"]["median_s"]
+    line["factorization"] = fac
+    if "fp64" in res and "mixed_fp32_ir" in res:
+        line["speedup_mixed_over_fp64"] = res["fp64"]["median_s"] / res["mixed_fp32_ir"]["median_s"]
     print(json.dumps(line))
     return 0
 
@@ -330,7 +360,7 @@ def run_step1(args):
     torch.cuda.set_device(0)
     L = q.lib()
     nb, ib = args.nb or 128, args.ib or 8
-    prec = 1 if args.prec == "f32" else 0
+    prec = {"f64": 0, "f32": 1, "tf32": 2, "bf16x3": 3}[args.prec]
     b = ctypes.c_int64()
     q._lib.check(L.qr_step1_workspace(nb, prec, 0, ctypes.byref(b)), "qr_step1_workspace")
     work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
@@ -363,7 +393,8 @@ def main():
     ap.add_argument("--ib", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--prec", default="f64", choices=["f64", "f32"], help="step1: precision of the TSMQR batch")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32", "tf32", "bf16x3"],
+                    help="step1: precision of the TSMQR batch (tf32 / bf16x3: FP32 tiles, tensor-core products)")
     ap.add_argument("--workload", default="qr", choices=["qr", "batched", "ls", "step1"],
                     help="qr: the headline line; batched / ls: the extension workloads (own JSON lines)")
     ap.add_argument("--count", type=int, default=4096)
@@ -372,6 +403,8 @@ def main():
     ap.add_argument("--ls-tol", type=float, default=1e-11,
                     help="mixed solve: stop once ||dx|| <= tol ||x|| (FP64-level accuracy for kappa 1e6)")
     ap.add_argument("--ls-p", type=int, default=0, help="panel domains of the solve's factorization (0 = the tuned table's p)")
+    ap.add_argument("--ls-precs", default="fp64,fp32,bf16x3",
+                    help="least-squares solves to time: fp64, fp32 (augmented IR), fp32_gmres, bf16x3, tf32 (GMRES-IR)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -458,7 +458,9 @@ int64_t qr_tune_nearest(int64_t value, const int64_t *grid, int ngrid);
  * operand copy l mod c, with c copies covering at least two L2 capacities
  * plus one copy, at least 2: each launch reads its operands from HBM).
  * launches <= 0 picks the count from one timed launch: enough launches for
- * about 30 ms, at least 3 and at most the paper's 50.
+ * about 30 ms, at least 3 and at most the paper's 50. prec QR_PREC_TF32 /
+ * QR_PREC_BF16X3 time the FP32 task with its products on the tensor cores
+ * (the update of qr_factor_mixed_s).
  * *seconds_per_launch, and *gflops (may be NULL) = batch x 4 NB^3 / time.
  */
 int qr_step1_workspace(int nb, int prec, int flush, int64_t *bytes);

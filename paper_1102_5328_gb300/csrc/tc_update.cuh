@@ -351,44 +351,72 @@ __device__ bool apply_qt_mma_staged(const float* __restrict__ V, int ldv, const 
   const size_t nv = (size_t)nrefP * L.ldvs, nt = (size_t)IB * nref, nc = TS ? (size_t)nref * ldcs : 0;
   // partial Y^T always go to part, never to wbuf: a warp may start the next
   // block's product 1 while another still reads W from wbuf in product 2
-  const size_t np = (size_t)L.WR * L.IBP * L.cw, nw = (size_t)L.IBP * L.ldw;
-  if (L.RW > 64 || (nv + nt + nc + np + nw) * sizeof(float) > dyn_smem_bytes()) return false;
+  // part and ysum rows padded by 8: the tpc threads of a column read rows
+  // q, q + 1, ... of one column at once, 8 banks apart
+  const int ldp = L.cw + 8;
+  const size_t np = (size_t)L.WR * L.IBP * ldp, nw = (size_t)L.IBP * L.ldw, ny = (size_t)L.IBP * ldp;
+  if (L.RW > 64 || (nv + nt + nc + np + nw + ny) * sizeof(float) > dyn_smem_bytes()) return false;
   float* vbuf = smem;
   float* tsb = vbuf + nv;
   float* ctop = tsb + nt;
   float* part = ctop + nc;
   float* wbuf = part + np;
+  float* ysum = wbuf + nw;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
   const int wm = warp % L.WM, wr = warp / L.WM;
   const int rw0 = wr * L.RW;
   const int NJ = L.RW / 8;
   // reflectors: float4 loads down each column (rows < `rows` only; the tile
-  // column holds NB >= rows rounded up to 4 elements), masks applied in
-  // registers, zero padding to nrefP x rowsPad
+  // column holds NB >= rows rounded up to 4 elements), all of a thread's
+  // loads in flight before its stores; masks applied in registers; zero
+  // padding to nrefP x rowsPad. Then the T factors, 8 loads in flight.
   {
     const int q4 = L.rowsPad / 4;
-    for (int idx = tid; idx < nrefP * q4; idx += NTHREADS) {
-      const int p = idx / q4, r = 4 * (idx - p * q4);
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (p < nref && r < rows) {
-        v = __ldcg(reinterpret_cast<const float4*>(V + r + (size_t)p * ldv));
-        float* e = &v.x;
+    const int tot = nrefP * q4;
+    for (int base = tid; base < tot; base += 4 * NTHREADS) {
+      float4 v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int rr = r + u;
-          if (rr >= rows) e[u] = 0.f;
-          else if (!TS) e[u] = rr < p ? 0.f : (rr == p ? 1.f : e[u]);
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * NTHREADS;
+        const int p = idx / q4, r = 4 * (idx - p * q4);
+        v[u] = (idx < tot && p < nref && r < rows) ? __ldcg(reinterpret_cast<const float4*>(V + r + (size_t)p * ldv))
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * NTHREADS;
+        if (idx < tot) {
+          const int p = idx / q4, r = 4 * (idx - p * q4);
+          float* e = &v[u].x;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int rr = r + c;
+            if (rr >= rows) e[c] = 0.f;
+            else if (!TS) e[c] = rr < p ? 0.f : (rr == p ? 1.f : e[c]);
+          }
+          *reinterpret_cast<float2*>(vbuf + (size_t)p * L.ldvs + r) = make_float2(v[u].x, v[u].y);
+          *reinterpret_cast<float2*>(vbuf + (size_t)p * L.ldvs + r + 2) = make_float2(v[u].z, v[u].w);
         }
       }
-      *reinterpret_cast<float2*>(vbuf + (size_t)p * L.ldvs + r) = make_float2(v.x, v.y);
-      *reinterpret_cast<float2*>(vbuf + (size_t)p * L.ldvs + r + 2) = make_float2(v.z, v.w);
     }
-    for (int idx = tid; idx < IB * nref; idx += NTHREADS) {
-      const int p = idx / IB, q = idx - p * IB;
-      tsb[idx] = ldg(T + q + (size_t)p * ldt);
+    const int tt = IB * nref;
+    for (int base = tid; base < tt; base += 8 * NTHREADS) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * NTHREADS;
+        const int p = idx / IB, q = idx - p * IB;
+        v[u] = idx < tt ? ldg(T + q + (size_t)p * ldt) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (base + u * NTHREADS < tt) tsb[base + u * NTHREADS] = v[u];
     }
   }
+  // the W phase: tpc threads per column (consecutive, so within one warp)
+  const int tpc = NTHREADS / L.cw;
+  const int wcol = tid / tpc, wsub = tid - (tid / tpc) * tpc;
   for (int cs = c0; cs < c1; cs += L.cw) {
     const int cwn = min(L.cw, c1 - cs);
     const int colA = wm * 16 + g, colB = colA + 8;
@@ -403,11 +431,23 @@ __device__ bool apply_qt_mma_staged(const float* __restrict__ V, int ldv, const 
       acc[j][2] = (in && okB && r < rows) ? ldg(C + r + (size_t)(cs + colB) * ldc) : 0.f;
       acc[j][3] = (in && okB && r + 1 < rows) ? ldg(C + r + 1 + (size_t)(cs + colB) * ldc) : 0.f;
     }
-    if (TS)
-      for (int idx = tid; idx < nref * L.cw; idx += NTHREADS) {
-        const int p = idx / L.cw, col = idx - p * L.cw;
-        ctop[p * ldcs + col] = col < cwn ? ldg(Ctop + p + (size_t)(cs + col) * ldct) : 0.f;
+    if (TS) {
+      const int tot = nref * L.cw;
+      for (int base = tid; base < tot; base += 8 * NTHREADS) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * NTHREADS;
+          const int p = idx / L.cw, col = idx - p * L.cw;
+          v[u] = (idx < tot && col < cwn) ? ldg(Ctop + p + (size_t)(cs + col) * ldct) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * NTHREADS;
+          if (idx < tot) ctop[(idx / L.cw) * ldcs + (idx - (idx / L.cw) * L.cw)] = v[u];
+        }
       }
+    }
     __syncthreads();  // staged reflectors, T and top rows visible
     for (int l0 = 0; l0 < nref; l0 += IB) {
       const int ib = min(IB, nref - l0);
@@ -460,46 +500,40 @@ __device__ bool apply_qt_mma_staged(const float* __restrict__ V, int ldv, const 
         }
       }
       {
-        float* dst = part + (size_t)wr * L.IBP * L.cw;
+        float* dst = part + (size_t)wr * L.IBP * ldp;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           if (q * 8 < L.IBP) {
             const int p0 = q * 8 + 2 * t;
-            dst[p0 * L.cw + colA] = y[q][0];
-            dst[(p0 + 1) * L.cw + colA] = y[q][1];
-            dst[p0 * L.cw + colB] = y[q][2];
-            dst[(p0 + 1) * L.cw + colB] = y[q][3];
+            dst[p0 * ldp + colA] = y[q][0];
+            dst[(p0 + 1) * ldp + colA] = y[q][1];
+            dst[p0 * ldp + colB] = y[q][2];
+            dst[(p0 + 1) * ldp + colB] = y[q][3];
           }
       }
       __syncthreads();
-      // --- W = T_l^T (Y + top rows), top rows -= W: one thread per column
-      if (tid < L.cw) {
-        const int col = tid;
-        float yv[32];
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
+      // --- W = T_l^T (Y + top rows), top rows -= W: the tpc threads of a
+      // column (one warp) sum Y(q) for q = wsub, wsub + tpc, ... (partials
+      // of the row warps, plus the top rows in TS mode) into ysum, then form
+      // W(p) for p = wsub, wsub + tpc, ...
+      {
+        const int col = wcol;
+        for (int q = wsub; q < ib; q += tpc) {
           float sum = 0.f;
-          if (q < ib) {
-            for (int w2 = 0; w2 < L.WR; ++w2) sum += part[((size_t)w2 * L.IBP + q) * L.cw + col];
-            if (TS) sum += ctop[(l0 + q) * ldcs + col];
-          }
-          yv[q] = sum;
+          for (int w2 = 0; w2 < L.WR; ++w2) sum += part[((size_t)w2 * L.IBP + q) * ldp + col];
+          if (TS) sum += ctop[(l0 + q) * ldcs + col];
+          ysum[q * ldp + col] = sum;
         }
+        __syncwarp();  // Y complete for this column; its top rows are read
         const float* tb = tsb + (size_t)l0 * IB;  // T(q, p) of this block at tb[q + p * IB]
-#pragma unroll
-        for (int pp = 31; pp >= 0; --pp) {
-          // descending p, so yv[p] still holds Y(p) when W(p) is formed
-          if (pp < ib) {
-            float wv = 0.f;
-#pragma unroll
-            for (int q = 0; q <= pp; ++q) wv = fmaf(tb[q + pp * IB], yv[q], wv);
-            if (TS) ctop[(l0 + pp) * ldcs + col] -= wv;
-            wbuf[pp * L.ldw + col] = wv;
-          }
+        for (int pp = wsub; pp < ib; pp += tpc) {
+          const float* tcol = tb + (size_t)pp * IB;
+          float wv = 0.f;
+          for (int q = 0; q <= pp; ++q) wv = fmaf(tcol[q], ysum[q * ldp + col], wv);
+          if (TS) ctop[(l0 + pp) * ldcs + col] -= wv;
+          wbuf[pp * L.ldw + col] = wv;
         }
-#pragma unroll
-        for (int pp = 0; pp < 32; ++pp)
-          if (pp >= ib && pp < L.IBP) wbuf[pp * L.ldw + col] = 0.f;
+        for (int pp = ib + wsub; pp < L.IBP; pp += tpc) wbuf[pp * L.ldw + col] = 0.f;
       }
       __syncthreads();
       // --- product 2: C^T -= W^T V_l^T

@@ -204,14 +204,15 @@ __global__ void fill_uniform(S* p, int64_t n, uint64_t seed, double lo, double h
   }
 }
 
-// Step-1 kernel: CTA b applies one TSMQR (V, T shared) to its own tile pair.
+// Step-1 kernel: CTA b applies one TSMQR (V, T shared) to its own tile pair;
+// tc (FP32 tiles) selects the tensor-core update of the mixed precisions.
 template <typename S>
 __global__ void __launch_bounds__(NTHREADS, 2)
-    tsmqr_batch(const S* V, const S* T, S* C1, S* C2, int NB, int IB) {
+    tsmqr_batch(const S* V, const S* T, S* C1, S* C2, int NB, int IB, int tc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Smem<S> sm = carve<S>(reinterpret_cast<S*>(smem_raw));
   const size_t te = (size_t)NB * NB;
-  tsmqr<S>(V, NB, T, IB, NB, NB, C1 + blockIdx.x * te, NB, C2 + blockIdx.x * te, NB, 0, NB, sm);
+  tsmqr<S>(V, NB, T, IB, NB, NB, C1 + blockIdx.x * te, NB, C2 + blockIdx.x * te, NB, 0, NB, sm, false, tc);
 }
 
 int sm_count() {
@@ -276,7 +277,7 @@ Step1Set<S> step1_set(void* work, int nb, int nbatch, int k) {
 // l mod nsets (step1_flush_sets), so its data is never in L2.
 template <typename S>
 int step1_time(int nb, int ib, int nbatch, int launches, int flush, double* sec, void* work, int64_t wbytes,
-               cudaStream_t st) {
+               cudaStream_t st, int tc = TC_NONE) {
   const int nsets = flush ? step1_flush_sets(nb, nbatch, sizeof(S)) : 1;
   if ((int64_t)nsets * step1_bytes(nb, nbatch, sizeof(S)) > wbytes) return -7;
   const size_t te = (size_t)nb * nb;
@@ -286,14 +287,15 @@ int step1_time(int nb, int ib, int nbatch, int launches, int flush, double* sec,
     fill_uniform<S><<<1024, 256, 0, st>>>(o.T, (int64_t)te, 12 + 16 * k, 0.0, 0.05);
     fill_uniform<S><<<1024, 256, 0, st>>>(o.C1, (int64_t)(2 * nbatch * te), 13 + 16 * k, -0.5, 0.5);
   }
-  const size_t smem = smem_elems<S>() * sizeof(S);
+  const size_t smem = (sizeof(S) == 4 && tc != TC_NONE) ? std::max<size_t>(smem_elems<S>() * sizeof(S), TC_SMEM_BYTES)
+                                                       : smem_elems<S>() * sizeof(S);
   cudaError_t e = cudaFuncSetAttribute(tsmqr_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   int cur = 0;
   auto launch = [&]() {
     const Step1Set<S> o = step1_set<S>(work, nb, nbatch, cur);
     cur = (cur + 1) % nsets;
-    tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(o.V, o.T, o.C1, o.C2, nb, ib);
+    tsmqr_batch<S><<<nbatch, NTHREADS, smem, st>>>(o.V, o.T, o.C1, o.C2, nb, ib, tc);
   };
   launch();  // warm-up
   cudaEvent_t e0, e1;
@@ -780,9 +782,10 @@ int64_t qr_tune_nearest(int64_t value, const int64_t* grid, int ngrid) {
 
 int qr_step1_workspace(int nb, int prec, int flush, int64_t* bytes) {
   if (nb < 8 || nb > 512) return -1;
+  if (prec < QR_PREC_F64 || prec > QR_PREC_BF16X3) return -2;
   if (flush != 0 && flush != 1) return -3;
   if (!bytes) return -4;
-  const size_t esz = prec == QR_PREC_F32 ? 4 : 8;
+  const size_t esz = prec == QR_PREC_F64 ? 8 : 4;
   *bytes = flush ? step1_flush_bytes(nb, 2 * sm_count(), esz) : step1_bytes(nb, 2 * sm_count(), esz);
   return 0;
 }
@@ -791,7 +794,7 @@ int qr_step1_time(int nb, int ib, int prec, int launches, int flush, double* sec
                   void* d_work, int64_t work_bytes, void* stream) {
   if (nb < 8 || nb > 512) return -1;
   if (ib < 1 || ib > nb || ib > 256) return -2;
-  if (prec != QR_PREC_F64 && prec != QR_PREC_F32) return -3;
+  if (prec < QR_PREC_F64 || prec > QR_PREC_BF16X3) return -3;
   if (flush != 0 && flush != 1) return -5;
   if (!seconds_per_launch) return -6;
   const int nbatch = 2 * sm_count();
@@ -799,7 +802,8 @@ int qr_step1_time(int nb, int ib, int prec, int launches, int flush, double* sec
   const int rc =
       prec == QR_PREC_F64
           ? step1_time<double>(nb, ib, nbatch, launches, flush, &s, d_work, work_bytes, (cudaStream_t)stream)
-          : step1_time<float>(nb, ib, nbatch, launches, flush, &s, d_work, work_bytes, (cudaStream_t)stream);
+          : step1_time<float>(nb, ib, nbatch, launches, flush, &s, d_work, work_bytes, (cudaStream_t)stream,
+                              tc_of_prec(prec));
   if (rc) return rc;
   *seconds_per_launch = s;
   if (gflops) *gflops = nbatch * 4.0 * nb * (double)nb * nb / s / 1e9;
