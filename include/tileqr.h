@@ -59,8 +59,11 @@ extern "C" {
 #define QR_OPT_UNMQR_WEIGHT    9 /* list schedule: UNMQR cost as a percentage of its flops (default 100) */
 #define QR_OPT_LS_REFINE      10 /* qr_solve_ls refinement: 0 automatic (F32 augmented, TF32/BF16X3 GMRES-IR), 1 augmented, 2 GMRES-IR */
 #define QR_OPT_GMRES_MAX      11 /* GMRES-IR: Krylov dimension per refinement step (default 50, at most QR_GMRES_MAX_DIM) */
-#define QR_OPT_GMRES_TOL_EXP  12 /* GMRES-IR: inner relative residual target 10^-value (default 10) */
+#define QR_OPT_GMRES_TOL_EXP  12 /* GMRES-IR: inner relative residual target 10^-value (default 6) */
 #define QR_GMRES_MAX_DIM      64
+#define QR_OPT_SM_BUDGET      13 /* SMs the persistent factorizations may use (0 = all): the grid is capped at that many
+                                    SMs' worth of CTAs and the list schedule plans for as many workers -- the GPU
+                                    counterpart of the paper's core count (Sec. 5.1); qr_tune records it per entry */
 
 /*
  * qr_workspace -- sizes of the caller-owned buffers of qr_factor_*.
@@ -324,14 +327,15 @@ int qr_batched_status(const void *d_scratch, int *status, void *stream);
  *   QR_OPT_GMRES_MAX iterations -- needed where kappa(A) u > 1 for the
  *   factorization's precision (TF32: u = 2^-11, BF16X3: about 2^-17, so
  *   kappa = 1e6 is beyond plain refinement). Stops when every column has
- *   ||dx|| <= tol ||x|| or after max_iter steps.
+ *   ||dx|| <= tol ||x||, when the corrections stop shrinking (augmented:
+ *   none halves any more from step 3 on; GMRES-IR: none shrinks tenfold
+ *   from step 2 on), or after max_iter steps.
  * nb, ib: tile order / inner blocking of the factorization (0 = tuned table).
  * p: panel domains of the factorization (qr_factor_p_*); 0 picks
  *   ceil(MT / NT) tile-row ranges per panel, at most 32 (1 = flat tree).
  * info[4] (may be NULL): refinement steps taken (max over RHS groups); 1 if
  *   every column met ||dx|| <= tol ||x|| (1 also for a plain solve), 2 if
- *   the corrections stopped shrinking (no column's correction fell below
- *   half the previous one, from the third step on: the limiting accuracy of
+ *   the corrections stopped shrinking as above (the limiting accuracy of
  *   FP64 residuals is reached), 0 if max_iter ran out first; device status
  *   bits (QR_DEV_*: of the factorization, and QR_DEV_TIMEOUT from the
  *   triangular solves, whose row blocks wait on each other with the same

@@ -49,11 +49,12 @@ int g_wunmqr = 100;  // list-schedule cost of UNMQR, percent of its flops
 // flop-count weights of the list schedule for that configuration
 std::map<std::tuple<int, int, int>, std::array<double, 4>> g_costs;
 int g_grid_limit = 0;
+int g_sm_budget = 0;  // QR_OPT_SM_BUDGET: SMs' worth of persistent CTAs (0 = all)
 int64_t g_drop_task = -1;
 int g_record = 0;
 int g_ls_refine = 0;     // QR_OPT_LS_REFINE
 int g_gmres_max = 50;    // QR_OPT_GMRES_MAX
-int g_gmres_tol_exp = 10;  // QR_OPT_GMRES_TOL_EXP
+int g_gmres_tol_exp = 6;  // QR_OPT_GMRES_TOL_EXP
 cudaEvent_t g_ev[2] = {nullptr, nullptr};
 bool g_ev_pending = false;
 
@@ -116,12 +117,29 @@ Layout make_layout(int64_t m, int64_t n, int nb, int ib, size_t esz) {
 // flop weights, then a stable sort on it. Dependencies always start strictly
 // earlier, so the result is a topological order.
 struct SchedKey {
-  int MT, NT, S, order;
+  int MT, NT, S, order, workers;
   double wG, wU, wT, wM;
   bool operator<(const SchedKey& o) const {
-    return std::tie(MT, NT, S, order, wG, wU, wT, wM) < std::tie(o.MT, o.NT, o.S, o.order, o.wG, o.wU, o.wT, o.wM);
+    return std::tie(MT, NT, S, order, workers, wG, wU, wT, wM) <
+           std::tie(o.MT, o.NT, o.S, o.order, o.workers, o.wG, o.wU, o.wT, o.wM);
   }
 };
+
+int device_sms() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  return sms;
+}
+
+// Persistent workers the list schedule plans for: two CTAs per SM of the SM
+// budget (g_mu held by the caller).
+int workers_locked() {
+  const int sms = device_sms();
+  return 2 * (g_sm_budget > 0 ? std::min(g_sm_budget, sms) : sms);
+}
 struct Sched {
   uint64_t* host = nullptr;  // pinned
   int64_t n = 0;
@@ -141,7 +159,7 @@ std::array<double, 4> task_weights(int prec, int nb, int ib, int S) {
 }
 
 const Sched& get_schedule(int MT, int NT, int S, const std::array<double, 4>& w) {
-  SchedKey key{MT, NT, S, g_order, w[0], w[1], w[2], w[3]};
+  SchedKey key{MT, NT, S, g_order, workers_locked(), w[0], w[1], w[2], w[3]};
   auto it = g_sched.find(key);
   if (it != g_sched.end()) return it->second;
   const int K = std::min(MT, NT);
@@ -230,12 +248,7 @@ const Sched& get_schedule(int MT, int NT, int S, const std::array<double, 4>& w)
   }
   std::vector<int64_t> idx;
   if (g_order == 1) {
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      cudaGetLastError();
-      sms = 152;
-    }
-    idx = list_schedule(wt, poff, pred, 2 * sms);
+    idx = list_schedule(wt, poff, pred, workers_locked());
   } else {
     idx.resize(code.size());
     std::iota(idx.begin(), idx.end(), 0);
@@ -381,6 +394,7 @@ int persistent_grid(int* grid_out, size_t smem) {
   int per = occ;
   if (g_ctas_per_sm > 0) per = std::min(per, g_ctas_per_sm);
   int grid = sms * per;
+  if (g_sm_budget > 0) grid = std::min(grid, std::min(g_sm_budget, sms) * per);
   if (g_grid_limit > 0) grid = std::min(grid, g_grid_limit);
   *grid_out = grid;
   return 0;
@@ -761,6 +775,10 @@ int qr_set_option(int opt, int64_t value) {
       if (value < 10 || value > 10000) return -2;
       g_wunmqr = (int)value;
       return 0;
+    case QR_OPT_SM_BUDGET:
+      if (value < 0 || value > 1 << 20) return -2;
+      g_sm_budget = (int)value;  // schedules are cached per worker count
+      return 0;
     case QR_OPT_LS_REFINE:
       if (value < 0 || value > 2) return -2;
       g_ls_refine = (int)value;
@@ -789,6 +807,7 @@ int64_t qr_get_option(int opt) {
     case QR_OPT_ORDER: return g_order;
     case QR_OPT_PANEL_WEIGHT: return g_wpanel;
     case QR_OPT_UNMQR_WEIGHT: return g_wunmqr;
+    case QR_OPT_SM_BUDGET: return g_sm_budget;
     case QR_OPT_LS_REFINE: return g_ls_refine;
     case QR_OPT_GMRES_MAX: return g_gmres_max;
     case QR_OPT_GMRES_TOL_EXP: return g_gmres_tol_exp;

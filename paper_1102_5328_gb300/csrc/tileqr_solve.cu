@@ -672,14 +672,19 @@ int correction(int64_t m, int64_t n, int nk, int nb, int ib, int p, const SolveL
 }
 
 // Outer stopping test shared by both refinement schemes: every column has
-// ||dx|| <= tol ||x|| (1), or no column's correction shrank by half any more
-// from the third step on: the accuracy of FP64 residuals is reached (2).
-int stop_test(int nk, int it, double tol, const std::vector<double>& hsq, std::vector<double>* prev) {
-  bool met = true, stalled = it >= 3;
+// ||dx|| <= tol ||x|| (1), or, from step `from` on, no column's correction
+// shrank below `ratio` times the previous one: the accuracy of FP64
+// residuals is reached (2). Augmented refinement contracts linearly (from
+// step 3, ratio 1/2); a GMRES-IR step solves the correction equation to a
+// small relative residual, so a productive step shrinks it by orders of
+// magnitude (from step 2, ratio 1/10).
+int stop_test(int nk, int it, double tol, const std::vector<double>& hsq, std::vector<double>* prev, int from,
+              double ratio) {
+  bool met = true, stalled = it >= from;
   for (int k = 0; k < nk; ++k) {
     const double dxn = std::sqrt(hsq[2 * k]);
     if (dxn > tol * std::sqrt(hsq[2 * k + 1])) met = false;
-    if (dxn <= 0.5 * (*prev)[k]) stalled = false;  // this column still converges
+    if (dxn <= ratio * (*prev)[k]) stalled = false;  // this column still converges
     (*prev)[k] = dxn;
   }
   return met ? 1 : (stalled ? 2 : 0);
@@ -714,7 +719,7 @@ int solve_group(int64_t m, int64_t n, int nk, const double* A, int64_t lda, cons
     if (max_iter <= 0) break;  // plain solve: one pass, no refinement test
     if ((e = cudaMemcpyAsync(hsq.data(), sq, 2 * nk * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return (int)e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return (int)e;
-    conv = stop_test(nk, it, tol, hsq, &prev);
+    conv = stop_test(nk, it, tol, hsq, &prev, 3, 0.5);
   }
   for (int k = 0; k < nk; ++k)
     if ((e = cudaMemcpyAsync(X + (size_t)k * ldx, x + (size_t)k * n, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) !=
@@ -835,7 +840,7 @@ int solve_group_gmres(int64_t m, int64_t n, int nk, const double* A, int64_t lda
     if (max_iter <= 0) break;  // one GMRES-preconditioned solve, no refinement test
     if ((e = cudaMemcpyAsync(hsq.data(), sq, 2 * nk * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return (int)e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return (int)e;
-    conv = stop_test(nk, it, tol, hsq, &prev);
+    conv = stop_test(nk, it, tol, hsq, &prev, 2, 0.1);
   }
   for (int k = 0; k < nk; ++k)
     if ((e = cudaMemcpyAsync(X + (size_t)k * ldx, x + (size_t)k * n, (size_t)n * 8, cudaMemcpyDeviceToDevice, st)) !=

@@ -92,15 +92,16 @@ int sched_workers() {
     cudaGetLastError();
     sms = 152;
   }
-  return 2 * sms;  // two persistent CTAs per SM
+  const int64_t budget = qr_get_option(QR_OPT_SM_BUDGET);
+  return 2 * (budget > 0 ? (int)std::min<int64_t>(budget, sms) : sms);  // two persistent CTAs per SM of the budget
 }
 
 struct DagKey {
-  int MT, NT, S, P, last_short;
+  int MT, NT, S, P, last_short, workers;
   double w0, w1, w2, w3;  // list-schedule weights (factorization DAGs)
   bool operator<(const DagKey& o) const {
-    return std::tie(MT, NT, S, P, last_short, w0, w1, w2, w3) <
-           std::tie(o.MT, o.NT, o.S, o.P, o.last_short, o.w0, o.w1, o.w2, o.w3);
+    return std::tie(MT, NT, S, P, last_short, workers, w0, w1, w2, w3) <
+           std::tie(o.MT, o.NT, o.S, o.P, o.last_short, o.workers, o.w0, o.w1, o.w2, o.w3);
   }
 };
 std::map<DagKey, Dag> g_dags;
@@ -109,7 +110,7 @@ std::map<DagKey, Dag> g_dags;
 // w: list-schedule costs of GEQRT, UNMQR, TSQRT, TSMQR (qr_task_weights);
 // the triangle-on-triangle tasks count half of their TS counterparts.
 const Dag& factor_dag(int MT, int NT, int S, int P, bool last_short, const std::array<double, 4>& w) {
-  DagKey key{MT, NT, S, P, last_short ? 1 : 0, w[0], w[1], w[2], w[3]};
+  DagKey key{MT, NT, S, P, last_short ? 1 : 0, sched_workers(), w[0], w[1], w[2], w[3]};
   auto it = g_dags.find(key);
   if (it != g_dags.end()) return it->second;
   const int K = std::min(MT, NT);
@@ -249,7 +250,7 @@ const Dag& factor_dag(int MT, int NT, int S, int P, bool last_short, const std::
 // Q application DAG over C's row blocks (column chunks S). Program order is
 // the factorization's update order for Q^T, reversed for Q.
 const Dag& apply_dag(int MT, int NT, int S, int P, bool last_short, int tr) {
-  DagKey key{MT, NT, S, -P - 1 - 1000 * tr, last_short ? 1 : 0, 0.0, 0.0, 0.0, 0.0};
+  DagKey key{MT, NT, S, -P - 1 - 1000 * tr, last_short ? 1 : 0, 0, 0.0, 0.0, 0.0, 0.0};
   auto it = g_dags.find(key);
   if (it != g_dags.end()) return it->second;
   const int K = std::min(MT, NT);
@@ -525,6 +526,8 @@ int factor_p_impl(int64_t m, int64_t n, S* A, int64_t lda, int nb, int ib, int p
   const int64_t cps = qr_get_option(QR_OPT_CTAS_PER_SM);
   if (cps > 0) per = std::min<int>(per, (int)cps);
   int grid = sms * per;
+  const int64_t budget = qr_get_option(QR_OPT_SM_BUDGET);
+  if (budget > 0) grid = std::min<int64_t>(grid, std::min<int64_t>(budget, sms) * per);
   const int64_t gl = qr_get_option(QR_OPT_GRID_LIMIT);
   if (gl > 0) grid = std::min<int>(grid, (int)gl);
   DagArgs<S> da;
