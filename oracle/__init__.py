@@ -10,7 +10,8 @@ Contents:
     Q, Q^T/Q application, back substitution, QR least squares, a
     doubled-precision augmented-system refinement (reference LS solution),
     long-double modified Gram-Schmidt (brute-force pin) and long-double
-    accuracy checks. Built with gcc into ``oracle/_build/liboracle.so``.
+    accuracy checks; the column-by-column Cholesky A = L L^T and its
+    long-double residual. Built with gcc into ``oracle/_build/liboracle.so``.
   * ``tuning.py`` -- the paper's pruning rules (Properties 4.1, 4.2, 5.1,
     Heuristics 0/1/2, nearest-point interpolation) as plain Python loops.
   * ``mlp.py`` -- fp64 numpy forward/backward/Adam of the cost-model MLP.
@@ -65,6 +66,9 @@ def lib():
         L.oracle_fact_residual.restype = ctypes.c_double
         L.oracle_orth_residual.argtypes = [i64, i64, dp, i64]
         L.oracle_orth_residual.restype = ctypes.c_double
+        L.oracle_potrf.argtypes = [i64, dp, i64]
+        L.oracle_chol_residual.argtypes = [i64, dp, i64, dp, i64]
+        L.oracle_chol_residual.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -185,6 +189,28 @@ def orth_residual(Q):
     Qc = _f64(Q)
     m, n = Qc.shape
     return lib().oracle_orth_residual(m, n, _p(Qc), m)
+
+
+def potrf(A):
+    """Cholesky A = L L^T by the column definition. Returns (L, info): L the
+    lower triangle (zero above), info 0 or the 1-based column whose pivot was
+    not positive."""
+    F = _f64(A)
+    n = F.shape[0]
+    info = lib().oracle_potrf(n, _p(F), max(n, 1))
+    return np.tril(F), info
+
+
+def chol_residual(A, L):
+    """||A - L L^T||_F / ||A||_F in long double (L: its lower triangle)."""
+    Ac, Lc = _f64(A), _f64(L)
+    n = Ac.shape[0]
+    return lib().oracle_chol_residual(n, _p(Ac), n, _p(Lc), n)
+
+
+def chol_flops(n):
+    """Credited flops of a Cholesky factorization, n^3 / 3."""
+    return float(n) ** 3 / 3.0
 
 
 def qr_flops(m, n):

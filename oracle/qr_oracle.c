@@ -344,3 +344,45 @@ double oracle_orth_residual(int64_t m, int64_t n, const double *Q, int64_t ldq) 
   }
   return (double)sqrtl(acc);
 }
+
+/* ---------------------------------------------------------------------------
+ * Cholesky factorization A = L L^T (the sister factorization the paper names
+ * for the same tile framework and tuner, Secs. 1 and 6), by its definition
+ * column by column: L_jj = sqrt(A_jj - sum_{k<j} L_jk^2), and for i > j
+ * L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj. In place on the lower triangle
+ * of A (n x n, lda); the strict upper triangle is left as it was. Returns 0,
+ * or j + 1 when the pivot of column j is not positive (A is not positive
+ * definite; columns >= j are then unchanged). */
+int oracle_potrf(int64_t n, double *A, int64_t lda) {
+  for (int64_t j = 0; j < n; ++j) {
+    double d = A[IDX(j, j, lda)];
+    for (int64_t k = 0; k < j; ++k) d -= A[IDX(j, k, lda)] * A[IDX(j, k, lda)];
+    if (!(d > 0.0)) return (int)(j + 1);
+    const double ljj = sqrt(d);
+    A[IDX(j, j, lda)] = ljj;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double s = A[IDX(i, j, lda)];
+      for (int64_t k = 0; k < j; ++k) s -= A[IDX(i, k, lda)] * A[IDX(j, k, lda)];
+      A[IDX(i, j, lda)] = s / ljj;
+    }
+  }
+  return 0;
+}
+
+/* ||A - L L^T||_F / ||A||_F in long double over the full symmetric A (both
+ * triangles of the n x n A are read; only the lower triangle of L). */
+double oracle_chol_residual(int64_t n, const double *A, int64_t lda, const double *L, int64_t ldl) {
+  long double num = 0.0L, den = 0.0L;
+#pragma omp parallel for reduction(+ : num, den) schedule(dynamic, 4)
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t i = 0; i < n; ++i) {
+      long double s = A[IDX(i, j, lda)];
+      den += s * s;
+      const int64_t kmax = i < j ? i : j;
+      for (int64_t k = 0; k <= kmax; ++k) s -= (long double)L[IDX(i, k, ldl)] * L[IDX(j, k, ldl)];
+      num += s * s;
+    }
+  }
+  return (double)(sqrtl(num) / sqrtl(den));
+}
