@@ -46,6 +46,7 @@ extern "C" {
 /* Device status bits (qr_status). */
 #define QR_DEV_TIMEOUT   1 /* a scheduler dependency wait ran out of time */
 #define QR_DEV_NONFINITE 2 /* a column norm or pivot was Inf/NaN */
+#define QR_DEV_NOT_SPD   4 /* Cholesky: a pivot was not positive (chol_status gives the first such column) */
 
 /* Options (qr_set_option). */
 #define QR_OPT_WAIT_TIMEOUT_US 1 /* per-wait limit of the persistent scheduler (default 20 s) */
@@ -380,10 +381,12 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t l
  *   tunes without a model): the learned cost model (qr_mlp_*), fitted on
  *   the GPU to the Step-2 timings of the orders already done (features
  *   log m, log n, NB/512, IB/256; target log seconds), ranks the survivors
- *   of each order from the third one on, and only the k it ranks fastest are
- *   timed; the search goes further down the ranking while the last pair
- *   timed is the fastest so far, and times every survivor when a prediction
- *   of a timed pair is off by more than a factor e^0.25. Measurements always
+ *   of each square order from the third square order on, and only the k it
+ *   ranks fastest are timed; the search goes further down the ranking while
+ *   the last pair timed is the fastest so far, and times every survivor when
+ *   the model's relative predictions are off (measured / predicted of a
+ *   timed pair differs from that of the top-ranked pair by more than a factor
+ *   e^0.25). Other shapes are timed in full. Measurements always
  *   decide; a survivor left untimed is not pruned. The final model, fitted
  *   to all Step-2 timings, is saved in the table ("model") and answers
  *   qr_model_propose. Predictions are logged as kind 4.
@@ -424,7 +427,9 @@ int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t *bytes);
  * qr_load_table / qr_clear_tables / qr_lookup -- the decision table. A
  * request for an untuned shape uses the closest tuned one (Sec. 5.1: the
  * closest benchmarked configuration), distance |m - m_i| + |n - n_i|, ties
- * to the smaller tuned shape; with no table the built-in pair (128, 16).
+ * to the smaller tuned shape, among the entries of the SM budget closest to
+ * QR_OPT_SM_BUDGET (see qr_lookup_sms); with no table the built-in pair
+ * (128, 16).
  * prec selects the fp64 or fp32 table (fp32 falls back to fp64's).
  */
 int qr_load_table(const char *path);
@@ -433,6 +438,18 @@ int qr_lookup(int64_t m, int64_t n, int prec, int *nb, int *ib);
 /* qr_lookup_p -- as qr_lookup, and *p the tuned panel domains for
  * qr_factor_p_* (1 where the table has none: the flat tree). */
 int qr_lookup_p(int64_t m, int64_t n, int prec, int *nb, int *ib, int *p);
+/*
+ * qr_lookup_sms -- the tuned (nb, ib, p) for an m x n problem on an SM
+ * budget of sms SMs (0 = the whole GPU), the GPU reading of the paper's
+ * (N, ncores) table (Sec. 5.1): the closest tuned budget first (ties to the
+ * smaller), then the closest tuned shape of that budget, as in the paper's
+ * example where N = 1800 on 5 cores takes the point tuned for N = 2000 on 4.
+ * Table entries carry the budget they were tuned under ("sms"; qr_tune
+ * records QR_OPT_SM_BUDGET, 0 = whole GPU). nb = 0 in qr_factor_* looks up
+ * with the current QR_OPT_SM_BUDGET. p may be NULL. TF32/BF16X3 use the fp32
+ * table. With no table: (128, 16, 1).
+ */
+int qr_lookup_sms(int64_t m, int64_t n, int prec, int sms, int *nb, int *ib, int *p);
 
 /*
  * Host-only decision rules of the tuner (no GPU call), exported so that they
@@ -508,6 +525,67 @@ int qr_mlp_grad(int nsamp, const float *d_X, const float *d_y, const float *d_pa
 int qr_mlp_adam_step(const float *d_grads, float *d_params, float *d_m, float *d_v, int t, float lr, void *stream);
 int qr_mlp_train(int nsamp, const float *d_X, const float *d_y, float *d_params, float *d_m, float *d_v, int steps,
                  float lr, float *d_grads, float *d_work, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Tile Cholesky A = L L^T on the same persistent scheduler, with its own
+ * empirical NB tuner (the paper names Cholesky and LU as the factorizations
+ * its framework and tuning method carry over to, Secs. 1 and 6; it tunes QR).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * chol_workspace / chol_factor_d -- FP64 tile Cholesky of the symmetric
+ * positive definite n x n matrix A (column-major, lda >= n; only its lower
+ * triangle is read). On return the lower triangle holds L; the strict upper
+ * triangle is not touched. nb: tile order, a multiple of 16 in [16, 256]
+ * (0 = the Cholesky tuning table, closest tuned order; 128 without one).
+ * Tasks POTRF(k), TRSM(i, k), SYRK(i, k), GEMM(i, j, k) over the tiles of
+ * the lower triangle run in one persistent kernel in a list-scheduled order,
+ * each waiting (bounded) on per-tile operation counters. d_scratch
+ * (chol_workspace bytes: the control block, counters, task list and the tile
+ * copy of A) is caller-owned. Queues: layout conversion, the persistent
+ * kernel, conversion of the lower triangle back. Errors: -1 n, -2 A, -3 lda,
+ * -4 nb, -5 no scratch, -6 scratch too small.
+ * chol_status: synchronises `stream`; *status gets the QR_DEV_* bits of the
+ * last factorization that used d_scratch (QR_DEV_NOT_SPD, QR_DEV_TIMEOUT),
+ * *first_bad_col (may be NULL) the smallest column whose pivot was not
+ * positive, or -1.
+ * chol_task_count_n: tasks of the DAG for (n, nb).
+ */
+int chol_workspace(int64_t n, int nb, int64_t *bytes);
+int chol_factor_d(int64_t n, double *d_A, int64_t lda, int nb, void *d_scratch, int64_t scratch_bytes, void *stream);
+int chol_status(const void *d_scratch, int *status, int64_t *first_bad_col, void *stream);
+int64_t chol_task_count_n(int64_t n, int nb);
+
+/*
+ * The Cholesky tuner (Secs. 4-5 applied to the one tuning parameter NB).
+ * chol_step1_time: Step 1 -- `launches` back-to-back launches (<= 0: enough
+ *   for ~30 ms, 3 to 50) of a batch of 2 x (SM count) independent GEMM tile
+ *   tasks C -= A B^T of order nb (the dominant task), same data every launch;
+ *   *gflops = batch x 2 nb^3 / time. Workspace: chol_step1_workspace.
+ * chol_time_factor: Step 2 measurement -- reps timed factorizations of a
+ *   device-generated symmetric matrix with entries uniform[-0.5, 0.5) and n
+ *   added to the diagonal (diagonally dominant, so positive definite),
+ *   regenerated before each run; median and minimum seconds. d_work holds
+ *   the matrix and the scratch (chol_tune_workspace for n covers it).
+ * chol_tune: Step 1 over NB in {32, 64, ..., 256}; the upper hull and
+ *   Heuristic `heuristic` (qr_tune_preselect); Step 2 over the orders ns[]
+ *   ascending, `reps` runs each, prune as you go (Property 5.1). table_path:
+ *   JSON decision table (entries n, nb, GFLOP/s credited n^3 / 3); it also
+ *   becomes the in-process table of nb = 0. log_path: JSONL of every
+ *   measurement (kind 11 Step 1, 12 Step 2), reused by a later run.
+ *   seconds_out[4]: total, Step 1, Step 2 seconds, factorizations timed.
+ * chol_load_table / chol_lookup: the decision table; closest tuned order.
+ */
+int chol_step1_workspace(int nb, int64_t *bytes);
+int chol_step1_time(int nb, int launches, double *seconds_per_launch, double *gflops, void *d_work, int64_t work_bytes,
+                    void *stream);
+int chol_time_factor(int64_t n, int nb, int reps, double *median_s, double *min_s, void *d_work, int64_t work_bytes,
+                     void *stream);
+int chol_tune_workspace(int64_t max_n, int64_t *bytes);
+int chol_tune(const int64_t *ns, int nshapes, int heuristic, int reps, const char *table_path, const char *log_path,
+              void *d_work, int64_t work_bytes, double *seconds_out, void *stream);
+int chol_load_table(const char *path);
+int chol_lookup(int64_t n, int *nb);
 
 /* qr_task_count -- number of tasks of the flat-tree factorization DAG at
  * precision prec (QR_PREC_*; the column split of the update tasks depends on

@@ -24,6 +24,7 @@ QR_PREC_TF32 = 2
 QR_PREC_BF16X3 = 3
 QR_DEV_TIMEOUT = 1
 QR_DEV_NONFINITE = 2
+QR_DEV_NOT_SPD = 4
 QR_OPT_WAIT_TIMEOUT_US = 1
 QR_OPT_CTAS_PER_SM = 2
 QR_OPT_SPLIT = 3
@@ -63,6 +64,9 @@ def lib():
                 for e in tab.get("entries", []):
                     c = (ctypes.c_double * 4)(*e["costs"])
                     L.qr_set_task_costs(prec, int(e["nb"]), int(e["ib"]), c)
+        path = os.path.join(_TUNED_DIR, "gb300_chol_fp64.json")
+        if os.path.exists(path):
+            L.chol_load_table(path.encode())
         path = os.path.join(_TUNED_DIR, "gb300_batched_classes.json")
         if os.path.exists(path):
             with open(path) as f:
@@ -398,6 +402,15 @@ def qr_lookup(m, n, dtype=torch.float64):
     return nb.value, ib.value
 
 
+def qr_lookup_sms(m, n, dtype=torch.float64, sms=0):
+    """(nb, ib, p) tuned for m x n on an SM budget of ``sms`` SMs (0 = the
+    whole GPU): the closest tuned budget, then the closest tuned shape."""
+    nb, ib, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _lib.check(lib().qr_lookup_sms(m, n, _prec(dtype), int(sms), ctypes.byref(nb), ctypes.byref(ib),
+                                   ctypes.byref(p)), "qr_lookup_sms")
+    return nb.value, ib.value, p.value
+
+
 def qr_lookup_p(m, n, dtype=torch.float64):
     """(nb, ib, p) from the loaded tuning table (built-in default otherwise)."""
     nb, ib, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -409,3 +422,56 @@ def qr_lookup_p(m, n, dtype=torch.float64):
 def qr_flops(m, n):
     """Credited flops 2mn^2 - 2n^3/3 (= 4/3 N^3 when m = n, Sec. 2.2)."""
     return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+class CholFactorization:
+    """Result of chol_factor: A with L in its lower triangle, the scratch
+    buffer (which holds the device status) and the tile order used."""
+
+    def __init__(self, A, scratch, nb):
+        self.A, self.scratch, self.nb = A, scratch, nb
+
+    def L(self):
+        return torch.tril(self.A)
+
+    def status(self, stream=None):
+        """(QR_DEV_* bits, first column whose pivot was not positive or -1)."""
+        st, col = ctypes.c_int(), ctypes.c_int64()
+        _lib.check(lib().chol_status(ctypes.c_void_p(self.scratch.data_ptr()), ctypes.byref(st), ctypes.byref(col),
+                                     _stream_ptr(stream)), "chol_status")
+        return st.value, col.value
+
+
+def chol_factor(A, nb=0, scratch=None, stream=None):
+    """Tile Cholesky of the SPD matrix A (float64, column-major CUDA tensor;
+    its lower triangle is read and overwritten with L). nb = 0 uses the
+    Cholesky tuning table."""
+    n = A.shape[0]
+    if A.dtype != torch.float64 or not A.is_cuda or A.stride(0) != 1 or A.shape[1] != n:
+        raise ValueError("A must be a square column-major float64 CUDA tensor")
+    if nb == 0:
+        nbv = ctypes.c_int()
+        _lib.check(lib().chol_lookup(n, ctypes.byref(nbv)), "chol_lookup")
+        nb = nbv.value
+    b = ctypes.c_int64()
+    _lib.check(lib().chol_workspace(n, nb, ctypes.byref(b)), "chol_workspace")
+    if scratch is None or scratch.numel() < b.value:
+        scratch = torch.empty(b.value, dtype=torch.uint8, device=A.device)
+    lda = A.stride(1) if n > 1 else max(n, 1)
+    _lib.check(lib().chol_factor_d(n, ctypes.c_void_p(A.data_ptr()), lda, nb, ctypes.c_void_p(scratch.data_ptr()),
+                                   b.value, _stream_ptr(stream)), "chol_factor_d")
+    return CholFactorization(A, scratch, nb)
+
+
+def chol_tune(ns, heuristic=2, reps=6, table="", log="", stream=None):
+    """The Cholesky NB tuner (chol_tune); returns its wall-time figures."""
+    L = lib()
+    b = ctypes.c_int64()
+    _lib.check(L.chol_tune_workspace(max(ns), ctypes.byref(b)), "chol_tune_workspace")
+    work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+    arr = (ctypes.c_int64 * len(ns))(*ns)
+    secs = (ctypes.c_double * 4)()
+    _lib.check(L.chol_tune(arr, len(ns), heuristic, reps, table.encode(), log.encode(), ctypes.c_void_p(work.data_ptr()),
+                           b.value, secs, _stream_ptr(stream)), "chol_tune")
+    return {"seconds": secs[0], "step1_seconds": secs[1], "step2_seconds": secs[2], "factorizations_timed": int(secs[3]),
+            "heuristic": heuristic, "reps": reps, "ns": list(ns), "table": table, "log": log}

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("qr_mlp_train", c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_int, ctypes.c_float, c_vp, c_vp, c_vp]),
     ("qr_clear_tables", c_int, []),
     ("qr_lookup", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    ("qr_lookup_sms", c_int, [c_i64, c_i64, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                              ctypes.POINTER(c_int)]),
     ("qr_lookup_p", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     ("qr_tune_grid", c_int, [c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     ("qr_tune_preselect", c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_dbl), c_int,
@@ -78,6 +80,18 @@ SIGNATURES = [
     ("qr_tune", c_int, [ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_int, c_int, c_int, c_int, c_int, c_int,
                         ctypes.c_char_p, ctypes.c_char_p, c_vp, c_i64, ctypes.POINTER(c_dbl), c_vp]),
     ("qr_factor_mixed_s", c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_int, c_vp, c_vp, c_i64, c_vp]),
+    ("chol_workspace", c_int, [c_i64, c_int, ctypes.POINTER(c_i64)]),
+    ("chol_factor_d", c_int, [c_i64, c_vp, c_i64, c_int, c_vp, c_i64, c_vp]),
+    ("chol_status", c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), c_vp]),
+    ("chol_task_count_n", c_i64, [c_i64, c_int]),
+    ("chol_step1_workspace", c_int, [c_int, ctypes.POINTER(c_i64)]),
+    ("chol_step1_time", c_int, [c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
+    ("chol_time_factor", c_int, [c_i64, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
+    ("chol_tune_workspace", c_int, [c_i64, ctypes.POINTER(c_i64)]),
+    ("chol_tune", c_int, [ctypes.POINTER(c_i64), c_int, c_int, c_int, ctypes.c_char_p, ctypes.c_char_p, c_vp, c_i64,
+                          ctypes.POINTER(c_dbl), c_vp]),
+    ("chol_load_table", c_int, [ctypes.c_char_p]),
+    ("chol_lookup", c_int, [c_i64, ctypes.POINTER(c_int)]),
     ("qr_model_propose", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
     ("qr_peak_fp64", c_int, [ctypes.POINTER(c_dbl), c_vp]),

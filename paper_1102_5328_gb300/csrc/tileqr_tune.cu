@@ -118,16 +118,47 @@ struct Entry {
   int64_t m, n;
   int nb, ib;
   double gflops;
-  int p;  // panel domains (1 = flat tree; tuned for tall-skinny shapes)
+  int p;    // panel domains (1 = flat tree; tuned for tall-skinny shapes)
+  int sms;  // SM budget the entry was tuned for (0 = the whole GPU)
 };
 std::mutex g_tmu;
 std::vector<Entry> g_table[2];  // [0] fp64, [1] fp32
 
-int lookup_entry(const std::vector<Entry>& t, int64_t m, int64_t n, int* nb, int* ib, int* pd) {
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  return sms;
+}
+
+// The closest tuned configuration (Sec. 5.1), one dimension after the other
+// as the paper's example reads (N = 1800 on 5 cores -> the point tuned for
+// N = 2000 on 4 cores): first the closest SM budget among the entries (ties
+// to the smaller), then among that budget's entries the closest shape,
+// distance |m - m_i| + |n - n_i| (ties to the smaller shape). sms <= 0 and
+// entries' sms = 0 both mean the whole GPU.
+int lookup_entry(const std::vector<Entry>& t, int64_t m, int64_t n, int sms, int* nb, int* ib, int* pd) {
   if (t.empty()) return 1;
+  int dev_sms = -1;
+  auto eff = [&](int b) {
+    if (b > 0) return b;
+    if (dev_sms < 0) dev_sms = device_sm_count();
+    return dev_sms;
+  };
+  const int want = eff(sms);
+  int bsel = -1;
+  for (const Entry& e : t) {
+    const int b = eff(e.sms);
+    if (bsel < 0 || std::abs(b - want) < std::abs(bsel - want) || (std::abs(b - want) == std::abs(bsel - want) && b < bsel))
+      bsel = b;
+  }
   int64_t best = INT64_MAX, bsum = INT64_MAX;
   int bi = -1;
   for (int i = 0; i < (int)t.size(); ++i) {
+    if (eff(t[i].sms) != bsel) continue;
     const int64_t d = std::llabs(t[i].m - m) + std::llabs(t[i].n - n);
     const int64_t s = t[i].m + t[i].n;
     if (d < best || (d == best && s < bsum)) {
@@ -148,8 +179,9 @@ bool write_table(const char* path, int prec, const std::vector<Entry>& t, const 
   if (!f) return false;
   fprintf(f, "{\n  \"prec\": \"%s\",\n%s  \"entries\": [\n", prec ? "fp32" : "fp64", extra.c_str());
   for (size_t i = 0; i < t.size(); ++i)
-    fprintf(f, "    {\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"p\": %d, \"gflops\": %.4f}%s\n",
-            (long long)t[i].m, (long long)t[i].n, t[i].nb, t[i].ib, t[i].p, t[i].gflops, i + 1 < t.size() ? "," : "");
+    fprintf(f, "    {\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"p\": %d, \"gflops\": %.4f, \"sms\": %d}%s\n",
+            (long long)t[i].m, (long long)t[i].n, t[i].nb, t[i].ib, t[i].p, t[i].gflops, t[i].sms,
+            i + 1 < t.size() ? "," : "");
   fprintf(f, "  ]\n}\n");
   fclose(f);
   return true;
@@ -172,12 +204,18 @@ bool read_table(const char* path, int* prec, std::vector<Entry>* t, std::string*
     Entry e;
     long long m, n;
     e.p = 1;
+    e.sms = 0;
     if (sscanf(s.c_str() + p, "{\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"p\": %d, \"gflops\": %lf", &m,
                &n, &e.nb, &e.ib, &e.p, &e.gflops) != 6 &&
         sscanf(s.c_str() + p, "{\"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"gflops\": %lf", &m, &n, &e.nb,
                &e.ib, &e.gflops) != 5)
       return false;
     if (e.p < 1) e.p = 1;
+    {
+      const size_t close = s.find('}', p);
+      const size_t k = s.find("\"sms\": ", p);
+      if (k != std::string::npos && k < close) e.sms = std::max(0, atoi(s.c_str() + k + 7));
+    }
     e.m = m;
     e.n = n;
     t->push_back(e);
@@ -606,8 +644,9 @@ struct LogKey {
   int64_t m, n;
   int nb, ib;
   int p;
+  int sms;  // SM budget of a Step-2 timing (0 = the whole GPU; Step 1 is always 0)
   bool operator<(const LogKey& o) const {
-    return std::tie(kind, m, n, nb, ib, p) < std::tie(o.kind, o.m, o.n, o.nb, o.ib, o.p);
+    return std::tie(kind, m, n, nb, ib, p, sms) < std::tie(o.kind, o.m, o.n, o.nb, o.ib, o.p, o.sms);
   }
 };
 
@@ -622,23 +661,25 @@ void read_log(const char* path, std::map<LogKey, double>* seen) {
     double sec;
     if (sscanf(line, "{\"kind\": %d, \"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"seconds\": %lf", &kind, &m,
                &n, &nb, &ib, &sec) == 6) {
-      int pd = 1;
+      int pd = 1, sb = 0;
       const char* pp = strstr(line, "\"p\": ");
       if (pp) pd = atoi(pp + 5);
-      (*seen)[LogKey{kind, m, n, nb, ib, pd}] = sec;
+      const char* ps = strstr(line, "\"sms\": ");
+      if (ps) sb = atoi(ps + 7);
+      (*seen)[LogKey{kind, m, n, nb, ib, pd, sb}] = sec;
     }
   }
   fclose(f);
 }
 
 void append_log(const char* path, int kind, int64_t m, int64_t n, int nb, int ib, double sec, double smin,
-                int reps, int pd = 1) {
+                int reps, int pd = 1, int sms = 0) {
   if (!path || !path[0]) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
   fprintf(f, "{\"kind\": %d, \"m\": %lld, \"n\": %lld, \"nb\": %d, \"ib\": %d, \"seconds\": %.9g, \"min\": %.9g, "
-             "\"reps\": %d, \"p\": %d}\n",
-          kind, (long long)m, (long long)n, nb, ib, sec, smin, reps, pd);
+             "\"reps\": %d, \"p\": %d, \"sms\": %d}\n",
+          kind, (long long)m, (long long)n, nb, ib, sec, smin, reps, pd, sms);
   fclose(f);
 }
 
@@ -646,11 +687,12 @@ void append_log(const char* path, int kind, int64_t m, int64_t n, int nb, int ib
 
 // ---------------------------------------------------------------------------
 int qr_table_lookup(int64_t m, int64_t n, int elem_bytes, int* nb, int* ib, int* pd) {
+  const int sms = (int)qr_get_option(QR_OPT_SM_BUDGET);  // read before g_tmu: never both locks at once
   std::lock_guard<std::mutex> lock(g_tmu);
   const int p = elem_bytes == 4 ? 1 : 0;
   if (pd) *pd = 1;
-  if (lookup_entry(g_table[p], m, n, nb, ib, pd) == 0) return 0;
-  if (p == 1 && lookup_entry(g_table[0], m, n, nb, ib, pd) == 0) return 0;
+  if (lookup_entry(g_table[p], m, n, sms, nb, ib, pd) == 0) return 0;
+  if (p == 1 && lookup_entry(g_table[0], m, n, sms, nb, ib, pd) == 0) return 0;
   *nb = 128;  // built-in default when nothing is loaded
   *ib = 16;
   return 0;
@@ -715,6 +757,25 @@ int qr_lookup(int64_t m, int64_t n, int prec, int* nb, int* ib) {
   if (!nb) return -4;
   if (!ib) return -5;
   return qr_table_lookup(m, n, prec == QR_PREC_F32 ? 4 : 8, nb, ib, nullptr);
+}
+
+int qr_lookup_sms(int64_t m, int64_t n, int prec, int sms, int* nb, int* ib, int* p) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (prec < QR_PREC_F64 || prec > QR_PREC_BF16X3) return -3;
+  if (sms < 0) return -4;
+  if (!nb) return -5;
+  if (!ib) return -6;
+  std::lock_guard<std::mutex> lock(g_tmu);
+  const int t = prec == QR_PREC_F64 ? 0 : 1;
+  int pd = 1;
+  if (lookup_entry(g_table[t], m, n, sms, nb, ib, &pd) != 0 && (t == 0 || lookup_entry(g_table[0], m, n, sms, nb, ib, &pd) != 0)) {
+    *nb = 128;
+    *ib = 16;
+    pd = 1;
+  }
+  if (p) *p = pd;
+  return 0;
 }
 
 int qr_lookup_p(int64_t m, int64_t n, int prec, int* nb, int* ib, int* p) {
@@ -865,6 +926,9 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
   if (work_bytes <= kModelBytes) return -12;
   const bool exhaustive = (mode & 1) != 0;
   const int flush = (mode >> 1) & 1;
+  // the SM budget (QR_OPT_SM_BUDGET) every Step-2 timing of this call runs
+  // under; 0 = the whole GPU. Step 1 is budget-independent, as in the paper.
+  const int budget = (int)std::min<int64_t>(qr_get_option(QR_OPT_SM_BUDGET), sm_count());
   cudaStream_t st = (cudaStream_t)stream;
   void* mwork = d_work;  // the cost model's buffers
   void* fwork = (char*)d_work + kModelBytes;
@@ -888,7 +952,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       nb[g] = grid[g].first;
       ib[g] = grid[g].second;
       double s = 0, gf = 0;
-      auto it = seen.find(LogKey{step1_kind, 0, 0, nb[g], ib[g], 1});
+      auto it = seen.find(LogKey{step1_kind, 0, 0, nb[g], ib[g], 1, 0});
       if (it != seen.end()) {
         s = it->second;
       } else {
@@ -913,7 +977,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
   std::vector<std::pair<int, int>> surv = cand;
   std::vector<Sample> train;  // Step-2 timings of the orders done so far
   double step2_s = 0;
-  int measured = 0, done = 0, fallbacks = 0;
+  int measured = 0, done = 0, squares_done = 0, fallbacks = 0;
   for (int oi : order) {
     const int64_t m = ms[oi], n = ns[oi];
     const size_t ns_ = surv.size();
@@ -921,7 +985,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
     std::vector<char> have(ns_, 0);
     auto measure = [&](size_t c) -> int {
       double med = 0, mn = 0;
-      auto it = seen.find(LogKey{2, m, n, surv[c].first, surv[c].second, 1});
+      auto it = seen.find(LogKey{2, m, n, surv[c].first, surv[c].second, 1, budget});
       if (it != seen.end()) {
         med = it->second;
       } else {
@@ -929,7 +993,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
         int rc = qr_time_factor(m, n, surv[c].first, surv[c].second, prec, reps, &med, &mn, fwork, fbytes, stream);
         if (rc) return rc;
         step2_s += since(t0);
-        append_log(log_path, 2, m, n, surv[c].first, surv[c].second, med, mn, reps);
+        append_log(log_path, 2, m, n, surv[c].first, surv[c].second, med, mn, reps, 1, budget);
         ++measured;
       }
       sec[c] = med;
@@ -938,12 +1002,16 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       train.push_back(Sample{m, n, surv[c].first, surv[c].second, med});
       return 0;
     };
-    // With the model (use_model = k > 0, PSPAYG, from the third order on):
-    // fit it to the timings so far, rank the survivors by predicted time and
-    // measure the k best; keep going down the ranking while the last one
-    // measured is the fastest so far, and measure every survivor when a
-    // prediction of a measured pair is off by more than the trust margin.
-    const bool guided = use_model > 0 && !exhaustive && done >= 2 && (int)ns_ > use_model && train.size() >= 4;
+    // With the model (use_model = k > 0, PSPAYG, square orders from the
+    // third square order on): fit it to the timings so far, rank the
+    // survivors by predicted time and measure the k best; keep going down the
+    // ranking while the last one measured is the fastest so far, and measure
+    // every survivor when the model's relative predictions are off: the
+    // ratio measured / predicted of a timed pair differs from that of the
+    // top-ranked pair by more than the trust margin (the model ranks; the
+    // overall scale of an extrapolation to a larger order may drift).
+    const bool guided = use_model > 0 && !exhaustive && m == n && squares_done >= 2 && (int)ns_ > use_model &&
+                        train.size() >= 4;
     if (!guided) {
       for (size_t c = 0; c < ns_; ++c)
         if (int rc = measure(c)) return rc;
@@ -956,7 +1024,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       if (rc) return rc;
       model_s += since(t0);
       for (size_t c = 0; c < ns_; ++c)
-        append_log(log_path, 4, m, n, surv[c].first, surv[c].second, pred[c], pred[c], 0);
+        append_log(log_path, 4, m, n, surv[c].first, surv[c].second, pred[c], pred[c], 0, 1, budget);
       std::vector<size_t> rank(ns_);
       for (size_t c = 0; c < ns_; ++c) rank[c] = c;
       std::stable_sort(rank.begin(), rank.end(), [&](size_t a, size_t b) { return pred[a] < pred[b]; });
@@ -972,8 +1040,9 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       while (r < ns_ && fastest() == rank[r - 1])
         if (int rc2 = measure(rank[r++])) return rc2;
       bool trusted = true;
-      for (size_t q = 0; q < r; ++q)
-        if (std::fabs(std::log(sec[rank[q]]) - std::log(pred[rank[q]])) > kModelTrust) trusted = false;
+      const double scale = std::log(sec[rank[0]]) - std::log(pred[rank[0]]);
+      for (size_t q = 1; q < r; ++q)
+        if (std::fabs(std::log(sec[rank[q]]) - std::log(pred[rank[q]]) - scale) > kModelTrust) trusted = false;
       if (!trusted) {
         ++fallbacks;
         for (; r < ns_; ++r)
@@ -984,14 +1053,14 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
     for (size_t c = 0; c < ns_; ++c)
       if (have[c] && (bi == ns_ || perf[c] > perf[bi] || (perf[c] == perf[bi] && surv[c].first < surv[bi].first)))
         bi = c;
-    Entry ent{m, n, surv[bi].first, surv[bi].second, perf[bi], 1};
+    Entry ent{m, n, surv[bi].first, surv[bi].second, perf[bi], 1, budget};
     // the paper's third tunable for tall-skinny matrices: the number of
     // panel domains, swept in powers of two with the chosen (NB, IB)
     const int64_t MTs = (m + ent.nb - 1) / ent.nb, NTs = (n + ent.nb - 1) / ent.nb;
     if (m >= 4 * n && MTs >= 4)
       for (int pd = 2; pd <= 64 && pd <= MTs / std::max<int64_t>(NTs, 1) * 2 && pd <= MTs; pd *= 2) {
         double med = 0, mn = 0;
-        auto it = seen.find(LogKey{3, m, n, ent.nb, ent.ib, pd});
+        auto it = seen.find(LogKey{3, m, n, ent.nb, ent.ib, pd, budget});
         if (it != seen.end()) {
           med = it->second;
         } else {
@@ -999,7 +1068,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
           int rc = qr_time_factor_p(m, n, ent.nb, ent.ib, pd, prec, reps, &med, &mn, fwork, fbytes, stream);
           if (rc) return rc;
           step2_s += since(t0);
-          append_log(log_path, 3, m, n, ent.nb, ent.ib, med, mn, reps, pd);
+          append_log(log_path, 3, m, n, ent.nb, ent.ib, med, mn, reps, pd, budget);
           ++measured;
         }
         const double g = qr_flops_d(m, n) / med / 1e9;
@@ -1032,6 +1101,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       surv = nx;
     }
     ++done;
+    if (m == n) ++squares_done;
   }
   // the final model, fitted to every Step-2 timing, proposes pairs for
   // untuned shapes (qr_model_propose) and is saved with the table

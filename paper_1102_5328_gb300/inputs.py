@@ -41,6 +41,13 @@ def conditioned_matrix(m, n, kappa, seed):
     return np.asfortranarray((U * sigma) @ V.T)
 
 
+def spd_matrix(n, seed):
+    """Symmetric positive definite n x n: G G^T / n + I with G (n x n) N(0,1)
+    from seed (eigenvalues in about [1, 5])."""
+    G = normal_matrix(n, n, seed)
+    return np.asfortranarray(G @ G.T / n + np.eye(n))
+
+
 def ls_problem(m, n, nrhs, kappa, seed):
     """(A, B): A from conditioned_matrix(seed), B (m x nrhs) N(0,1) from seed+1."""
     A = conditioned_matrix(m, n, kappa, seed)

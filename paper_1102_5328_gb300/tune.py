@@ -10,6 +10,9 @@ Properties 4.1/4.2 and Heuristic H0/H1/H2, then Step 2 with prune-as-you-go
 every shape). --flush: Step 1 as MultCallFlushLRU instead of No Flush.
 --use-model K: the learned cost model ranks the survivors from the third
 order on and only the K fastest-predicted are timed (see qr_tune).
+--sm-budgets B1,B2,...: Step 2 once per SM budget (QR_OPT_SM_BUDGET, the GPU
+counterpart of the paper's core counts, Sec. 5.1; 0 = the whole GPU), one
+log shared by all budgets (Step 1 runs once), the tables merged into --table.
 Shapes come from --ns (square) and --shapes (m x n list).
 Prints one JSON line with the wall times the library measured.
 """
@@ -34,6 +37,20 @@ def parse_shapes(ns, shapes):
                 m, n = s.lower().split("x")
                 out.append((int(m), int(n)))
     return out
+
+
+def write_table(path, tab):
+    """A decision table in the layout qr_load_table reads: one entry per line,
+    keys in the library's order."""
+    head = {k: v for k, v in tab.items() if k != "entries"}
+    lines = ["{"] + ["  %s: %s," % (json.dumps(k), json.dumps(v)) for k, v in head.items()]
+    lines.append('  "entries": [')
+    ents = [json.dumps({k: e[k] for k in ("m", "n", "nb", "ib", "p", "gflops", "sms") if k in e})
+            for e in tab["entries"]]
+    lines.append(",\n".join("    " + e for e in ents))
+    lines += ["  ]", "}"]
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
 
 
 def run(shapes, mode, heuristic, reps, prec, table, log, stream=None, use_model=0, flush=False):
@@ -75,12 +92,40 @@ def main(argv=None):
     ap.add_argument("--log", default="")
     ap.add_argument("--use-model", type=int, default=0)
     ap.add_argument("--flush", action="store_true")
+    ap.add_argument("--sm-budgets", default="", help="comma-separated SM budgets (0 = whole GPU)")
     a = ap.parse_args(argv)
     if a.table:
         os.makedirs(os.path.dirname(os.path.abspath(a.table)), exist_ok=True)
-    res = run(parse_shapes(a.ns, a.shapes), a.mode, a.heuristic, a.reps,
-              QR_PREC_F32 if a.prec == "f32" else QR_PREC_F64, a.table, a.log, use_model=a.use_model, flush=a.flush)
-    print(json.dumps(res))
+    prec = QR_PREC_F32 if a.prec == "f32" else QR_PREC_F64
+    shapes = parse_shapes(a.ns, a.shapes)
+    if not a.sm_budgets:
+        res = run(shapes, a.mode, a.heuristic, a.reps, prec, a.table, a.log, use_model=a.use_model, flush=a.flush)
+        print(json.dumps(res))
+        return 0
+    from . import QR_OPT_SM_BUDGET, qr_set_option
+    merged, runs = None, []
+    try:
+        for b in [int(v) for v in a.sm_budgets.split(",") if v]:
+            qr_set_option(QR_OPT_SM_BUDGET, b)
+            tb = (a.table or "tune_table.json") + ".sms%d" % b
+            r = run(shapes, a.mode, a.heuristic, a.reps, prec, tb, a.log, use_model=a.use_model, flush=a.flush)
+            r["sm_budget"] = b
+            runs.append(r)
+            t = json.load(open(tb))
+            if merged is None:
+                merged = t
+            else:
+                merged["entries"] += t["entries"]
+            os.remove(tb)
+    finally:
+        qr_set_option(QR_OPT_SM_BUDGET, 0)
+    merged["sm_budgets"] = [r["sm_budget"] for r in runs]
+    merged["seconds"] = sum(r["seconds"] for r in runs)
+    merged.pop("model", None)  # one model per budget run; not merged
+    if a.table:
+        write_table(a.table, merged)
+        lib().qr_load_table(a.table.encode())
+    print(json.dumps({"runs": runs, "table": a.table}))
     return 0
 
 

@@ -26,7 +26,11 @@ import numpy as np
 from . import lib
 
 
-def load_log(path):
+def load_log(path, sms=0):
+    """Step-1 timings {(nb, ib): s} and flat-tree Step-2 timings
+    {(m, n, nb, ib): (s, reps)} of the whole GPU (or of SM budget sms) from a
+    tuner log; the domain sweeps (kind 3), the model's predictions (kind 4)
+    and the flushed Step 1 (kind 5) are not timings of these."""
     step1, step2 = {}, {}
     with open(path) as f:
         for line in f:
@@ -35,7 +39,7 @@ def load_log(path):
             r = json.loads(line)
             if r["kind"] == 1:
                 step1[(r["nb"], r["ib"])] = r["seconds"]
-            else:
+            elif r["kind"] == 2 and r.get("sms", 0) == sms:
                 step2[(r["m"], r["n"], r["nb"], r["ib"])] = (r["seconds"], r.get("reps", 1))
     return step1, step2
 

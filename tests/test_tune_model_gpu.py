@@ -1,11 +1,12 @@
 """The learned cost model inside the empirical search (qr_tune with
 use_model = k), and the MultCallFlushLRU variant of Step 1, on the GPU.
 
-The model-guided Step 2 is replayed from the tuner's own log: at every order
-from the third on where the model ranked the survivors (logged predictions,
-kind 4), the pairs timed must be exactly the k predicted fastest, extended
-down the ranking while the last one timed was the fastest so far, and all of
-them when a timed pair's prediction was off by more than e^0.25. The decision
+The model-guided Step 2 is replayed from the tuner's own log: at every
+square order from the third on where the model ranked the survivors (logged
+predictions, kind 4), the pairs timed must be exactly the k predicted
+fastest, extended down the ranking while the last one timed was the fastest
+so far, and all of them when a timed pair's measured / predicted ratio
+differed from the top-ranked pair's by more than e^0.25. The decision
 table must be the best timed pair; survivors left untimed are not pruned
 (Property 5.1 needs a measurement). The saved model is evaluated by the
 oracle's fp64 forward pass: it fits the timings it was trained on, and
@@ -79,8 +80,9 @@ def _replay_guided(log, shapes, sms, k, step1_kind=1):
             while r < len(surv) and fastest() == timed[-1]:
                 timed.append(rank[r])
                 r += 1
-            if any(abs(math.log(sec2[(m, n) + surv[c]]) - math.log(pred[(m, n) + surv[c]])) > TRUST
-                   for c in timed):
+            scale = math.log(sec2[(m, n) + surv[timed[0]]]) - math.log(pred[(m, n) + surv[timed[0]]])
+            if any(abs(math.log(sec2[(m, n) + surv[c]]) - math.log(pred[(m, n) + surv[c]]) - scale) > TRUST
+                   for c in timed[1:]):
                 timed += rank[r:]
         else:
             timed = list(range(len(surv)))

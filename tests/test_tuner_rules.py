@@ -193,3 +193,66 @@ def test_read_trace_decodes_records():
     task, typ, sm, tt, tr, td = q.read_trace(buf, 3)
     assert task.tolist() == [5, 0, 7] and typ.tolist() == [3, 0, 5] and sm.tolist() == [17, 151, 2]
     assert tt.tolist() == [100, 0, 300] and tr.tolist() == [500, 50, 400] and td.tolist() == [1100, 600, 900]
+
+
+def _restore_tables(L):
+    """Put back the committed tuning tables (later tests may look pairs up)."""
+    L.qr_clear_tables()
+    tuned = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1102_5328_gb300", "tuned")
+    for name in ("gb300_fp64.json", "gb300_fp32.json"):
+        if os.path.exists(os.path.join(tuned, name)):
+            L.qr_load_table(os.path.join(tuned, name).encode())
+
+
+def _load_synthetic_table(L, tmp_path, entries, prec="fp64"):
+    path = tmp_path / "t.json"
+    rows = ",\n".join('    {"m": %d, "n": %d, "nb": %d, "ib": %d, "p": %d, "gflops": 1.0, "sms": %d}' % e for e in entries)
+    path.write_text('{\n  "prec": "%s",\n  "entries": [\n%s\n  ]\n}\n' % (prec, rows))
+    assert L.qr_load_table(str(path).encode()) == 0
+
+
+def _lookup_sms(L, m, n, sms):
+    nb, ib, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.qr_lookup_sms(m, n, 0, sms, ctypes.byref(nb), ctypes.byref(ib), ctypes.byref(p)) == 0
+    return nb.value, ib.value, p.value
+
+
+def test_sm_budget_lookup_is_the_papers_interpolation(L, tmp_path):
+    """The (N, SM budget) table read as the paper's (N, ncores) one: the
+    paper's example (N = 1800 on 5 cores -> the point tuned for N = 2000 on
+    4 cores) and random queries, against oracle.tuning.nearest applied to the
+    budget and then to N. Each grid point gets a distinct (nb, ib) so the
+    chosen entry is identified."""
+    grid_n = [500, 1000, 2000, 4000, 6000, 8000, 10000]
+    grid_c = [1, 2, 4, 8, 16, 32, 48]
+    ident = {}
+    entries = []
+    for a, n in enumerate(grid_n):
+        for b, c in enumerate(grid_c):
+            nb, ib = 64 + 32 * a, 8 + b
+            ident[(nb, ib)] = (n, c)
+            entries.append((n, n, nb, ib, 1, c))
+    try:
+        _load_synthetic_table(L, tmp_path, entries)
+        nb, ib, _ = _lookup_sms(L, 1800, 1800, 5)
+        assert ident[(nb, ib)] == (2000, 4)
+        rng = random.Random(5)
+        for _ in range(200):
+            n, c = rng.randint(100, 12000), rng.randint(1, 60)
+            nb, ib, _ = _lookup_sms(L, n, n, c)
+            assert ident[(nb, ib)] == (tuning.nearest(n, grid_n), tuning.nearest(c, grid_c)), (n, c)
+    finally:
+        _restore_tables(L)
+
+
+def test_sm_budget_lookup_with_whole_gpu_entries(L, tmp_path):
+    """Entries tuned without a budget (sms 0, the whole GPU) and a request
+    for the whole GPU (0) meet; a small budget takes its own entries."""
+    try:
+        _load_synthetic_table(L, tmp_path, [(1000, 1000, 64, 8, 1, 0), (1000, 1000, 96, 16, 1, 8),
+                                            (4000, 4000, 128, 8, 1, 0)])
+        assert _lookup_sms(L, 3900, 3900, 0)[:2] == (128, 8)
+        assert _lookup_sms(L, 3900, 3900, 6)[:2] == (96, 16)  # budget 8 is closest; its only entry
+        assert _lookup_sms(L, 900, 900, 10000)[:2] == (64, 8)  # beyond the GPU: the whole-GPU entries
+    finally:
+        _restore_tables(L)
