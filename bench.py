@@ -1,7 +1,7 @@
 """Benchmark of the FP64 tile Householder QR on one GB300 (or N replicas).
 
 Workload: square FP64 tile QR of order N = 10000 (the largest order of the
-paper's Step-2 discretization, Sec. 5.1), entries uniform[-0.5, 0.5) from a
+paper's Step-2 discretization, Sec. 6.1), entries uniform[-0.5, 0.5) from a
 seed, with the (NB, IB) pair of the tuning table (or --nb/--ib).
 A step = restore A from a pristine device copy, then qr_factor_d (layout
 conversion, the persistent DAG kernel, conversion back). Inputs (800 MB)
@@ -408,7 +408,7 @@ def run_cholesky(args):
 
 
 def run_step1(args):
-    """The Step-1 kernel benchmark (Sec. 4) for one (NB, IB): a batch of
+    """The Step-1 kernel benchmark (Sec. 5) for one (NB, IB): a batch of
     2 x SMs independent TSMQR tasks per launch, No Flush; GFLOP/s credits
     4 NB^3 per task."""
     import ctypes

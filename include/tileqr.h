@@ -64,7 +64,7 @@ extern "C" {
 #define QR_GMRES_MAX_DIM      64
 #define QR_OPT_SM_BUDGET      13 /* SMs the persistent factorizations may use (0 = all): the grid is capped at that many
                                     SMs' worth of CTAs and the list schedule plans for as many workers -- the GPU
-                                    counterpart of the paper's core count (Sec. 5.1); qr_tune records it per entry */
+                                    counterpart of the paper's core count (Sec. 6.1); qr_tune records it per entry */
 
 /*
  * qr_workspace -- sizes of the caller-owned buffers of qr_factor_*.
@@ -85,7 +85,7 @@ int qr_workspace(int64_t m, int64_t n, int nb, int ib, int prec, int64_t *t_elem
  *   reflectors below it (tile-QR storage: GEQRT's V below the diagonal of
  *   each diagonal tile, TSQRT's V filling each tile below it).
  * nb, ib: tile order and inner blocking; nb = 0 picks (nb, ib) from the
- *   tuning table loaded by qr_tune / qr_load_table (nearest tuned N, Sec. 5.1).
+ *   tuning table loaded by qr_tune / qr_load_table (nearest tuned N, Sec. 6.1).
  * d_T (t_elems from qr_workspace): the IB x NB triangular block factors.
  * d_scratch (scratch_bytes): caller-owned scratch; its status word is what
  *   qr_status reads.
@@ -152,7 +152,7 @@ int qr_apply_qt_ws_s(int64_t m, int64_t n, int64_t nrhs, const float *d_A, int64
 
 /*
  * Tile QR with p domains per panel (the paper's third tunable for
- * tall-skinny matrices, communication-avoiding QR, Sec. 6).
+ * tall-skinny matrices, communication-avoiding QR, Sec. 7).
  * qr_workspace_p / qr_factor_p_d / qr_factor_p_s: as qr_workspace /
  *   qr_factor_*, with p >= 1 domains: at step k the tile rows k..MT-1 are
  *   cut into ranges of ceil(MT/p) rows starting at row k (the domains slide
@@ -352,20 +352,20 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t l
                 void *d_work, int64_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
- * Empirical NB/IB autotuner (Secs. 4-5 of the paper).
+ * Empirical NB/IB autotuner (Secs. 5–6 of the paper).
  * ------------------------------------------------------------------------ */
 
 /*
- * qr_tune -- install-time tuning (Sec. 6: "make autotune", then an instant
+ * qr_tune -- install-time tuning (Sec. 7: "make autotune", then an instant
  * decision at call time). Shapes (ms[i], ns[i]), nshapes >= 1.
  * mode bit 0 = 0 (PSPAYG): Step 1 = time the TSMQR kernel (the paper's
  *   DSSRFB) for every (NB, IB) of the grid NB in {64..512 step 32}, IB | NB,
- *   8 <= IB <= NB/2 (119 pairs), up to 50 launches each (Sec. 4);
- *   Property 4.1 (best IB per NB), Property 4.2 (upper convex hull) and
+ *   8 <= IB <= NB/2 (119 pairs), up to 50 launches each (Sec. 5);
+ *   Property 5.1 (best IB per NB), Property 5.2 (upper convex hull) and
  *   Heuristic `heuristic` (0, 1 or 2; 2 is the paper's default) preselect at
  *   most 8 pairs; Step 2 = time qr_factor for the survivors at every shape,
- *   ascending n, `reps` runs each (median; the paper uses 6, Sec. 5.1), and
- *   prune as you go with Property 5.1 between square orders (Sec. 5.3).
+ *   ascending n, `reps` runs each (median; the paper uses 6, Sec. 6.1), and
+ *   prune as you go with Property 6.1 between square orders (Sec. 6.3).
  *   For tall-skinny shapes (m >= 4n, at least 4 tile rows) the chosen pair
  *   is then timed with p = 2, 4, ... panel domains (qr_factor_p_*; at most
  *   64 and 2 MT/NT), the paper's third tunable for such matrices; the
@@ -376,7 +376,7 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t l
  *   its own copy of the operands, taken in turn from enough copies that its
  *   data was last touched two L2 capacities ago (the paper reports "No
  *   Flush", where every launch reuses the same data, and leaves the flushing
- *   variants out of scope, Sec. 4). Logged as kind 5 instead of 1.
+ *   variants out of scope, Sec. 5). Logged as kind 5 instead of 1.
  * use_model = k in [1, 8] (0 = off; this library's addition, the paper
  *   tunes without a model): the learned cost model (qr_mlp_*), fitted on
  *   the GPU to the Step-2 timings of the orders already done (features
@@ -425,7 +425,7 @@ int qr_tune_workspace(int64_t max_m, int64_t max_n, int prec, int64_t *bytes);
 
 /*
  * qr_load_table / qr_clear_tables / qr_lookup -- the decision table. A
- * request for an untuned shape uses the closest tuned one (Sec. 5.1: the
+ * request for an untuned shape uses the closest tuned one (Sec. 6.1: the
  * closest benchmarked configuration), distance |m - m_i| + |n - n_i|, ties
  * to the smaller tuned shape, among the entries of the SM budget closest to
  * QR_OPT_SM_BUDGET (see qr_lookup_sms); with no table the built-in pair
@@ -441,7 +441,7 @@ int qr_lookup_p(int64_t m, int64_t n, int prec, int *nb, int *ib, int *p);
 /*
  * qr_lookup_sms -- the tuned (nb, ib, p) for an m x n problem on an SM
  * budget of sms SMs (0 = the whole GPU), the GPU reading of the paper's
- * (N, ncores) table (Sec. 5.1): the closest tuned budget first (ties to the
+ * (N, ncores) table (Sec. 6.1): the closest tuned budget first (ties to the
  * smaller), then the closest tuned shape of that budget, as in the paper's
  * example where N = 1800 on 5 cores takes the point tuned for N = 2000 on 4.
  * Table entries carry the budget they were tuned under ("sms"; qr_tune
@@ -456,13 +456,13 @@ int qr_lookup_sms(int64_t m, int64_t n, int prec, int sms, int *nb, int *ib, int
  * can be checked on their own:
  * qr_tune_grid -- the (NB, IB) grid (NB in nb_lo..nb_hi step nb_step, IB a
  *   divisor of NB in [ib_min, NB/2]); writes up to cap pairs, returns the count.
- * qr_tune_preselect -- Property 4.1, the upper hull (Property 4.2) and
+ * qr_tune_preselect -- Property 5.1, the upper hull (Property 5.2) and
  *   Heuristic 0/1/2 over npairs Step-1 results; writes the preselected
  *   pairs (ascending NB) and returns how many (<= max_sel for H1/H2;
  *   nseg iso-segments for H2).
- * qr_tune_payg -- Property 5.1: keep[a] = 0 iff some pair with larger NB has
+ * qr_tune_payg -- Property 6.1: keep[a] = 0 iff some pair with larger NB has
  *   strictly higher performance at the order just measured.
- * qr_tune_nearest -- the closest grid value (ties to the smaller), Sec. 5.1.
+ * qr_tune_nearest -- the closest grid value (ties to the smaller), Sec. 6.1.
  */
 int qr_tune_grid(int nb_lo, int nb_hi, int nb_step, int ib_min, int cap, int *nbs, int *ibs);
 int qr_tune_preselect(int npairs, const int *nb, const int *ib, const double *perf, int heuristic, int max_sel,
@@ -471,7 +471,7 @@ int qr_tune_payg(int nsurv, const int *nb, const double *perf, int *keep);
 int64_t qr_tune_nearest(int64_t value, const int64_t *grid, int ngrid);
 
 /*
- * qr_step1_workspace / qr_step1_time -- the Step-1 kernel benchmark of Sec. 4
+ * qr_step1_workspace / qr_step1_time -- the Step-1 kernel benchmark of Sec. 5
  * for one (nb, ib): `launches` back-to-back launches of a batch of
  * 2 x (SM count) independent TSMQR tile tasks, timed with CUDA events on
  * `stream`; synchronous. flush = 0: "No Flush" (same data every launch, the
@@ -504,7 +504,7 @@ int qr_time_factor_p(int64_t m, int64_t n, int nb, int ib, int p, int prec, int 
 
 /*
  * Learned cost model of the tuner (this library's addition; the paper tunes
- * without a model, Secs. 1 and 3). A 4 -> 64 -> 64 -> 1 perceptron with ReLU
+ * without a model, Secs. 1 and 2.3). A 4 -> 64 -> 64 -> 1 perceptron with ReLU
  * hidden layers, FP32, mapping standardized (log m, log n, NB/512, IB/256)
  * to log(seconds). d_params: QR_MLP_NPARAMS floats laid out W1 (64 x 4,
  * row-major [out][in]), b1 (64), W2 (64 x 64), b2 (64), W3 (1 x 64), b3 (1).
@@ -529,7 +529,7 @@ int qr_mlp_train(int nsamp, const float *d_X, const float *d_y, float *d_params,
 /* ------------------------------------------------------------------------
  * Tile Cholesky A = L L^T on the same persistent scheduler, with its own
  * empirical NB tuner (the paper names Cholesky and LU as the factorizations
- * its framework and tuning method carry over to, Secs. 1 and 6; it tunes QR).
+ * its framework and tuning method carry over to, Secs. 1 and 7; it tunes QR).
  * ------------------------------------------------------------------------ */
 
 /*
@@ -557,7 +557,7 @@ int chol_status(const void *d_scratch, int *status, int64_t *first_bad_col, void
 int64_t chol_task_count_n(int64_t n, int nb);
 
 /*
- * The Cholesky tuner (Secs. 4-5 applied to the one tuning parameter NB).
+ * The Cholesky tuner (Secs. 5–6 applied to the one tuning parameter NB).
  * chol_step1_time: Step 1 -- `launches` back-to-back launches (<= 0: enough
  *   for ~30 ms, 3 to 50) of a batch of 2 x (SM count) independent GEMM tile
  *   tasks C -= A B^T of order nb (the dominant task), same data every launch;
@@ -569,7 +569,7 @@ int64_t chol_task_count_n(int64_t n, int nb);
  *   the matrix and the scratch (chol_tune_workspace for n covers it).
  * chol_tune: Step 1 over NB in {32, 64, ..., 256}; the upper hull and
  *   Heuristic `heuristic` (qr_tune_preselect); Step 2 over the orders ns[]
- *   ascending, `reps` runs each, prune as you go (Property 5.1). table_path:
+ *   ascending, `reps` runs each, prune as you go (Property 6.1). table_path:
  *   JSON decision table (entries n, nb, GFLOP/s credited n^3 / 3); it also
  *   becomes the in-process table of nb = 0. log_path: JSONL of every
  *   measurement (kind 11 Step 1, 12 Step 2), reused by a later run.

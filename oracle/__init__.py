@@ -12,7 +12,7 @@ Contents:
     long-double modified Gram-Schmidt (brute-force pin) and long-double
     accuracy checks; the column-by-column Cholesky A = L L^T and its
     long-double residual. Built with gcc into ``oracle/_build/liboracle.so``.
-  * ``tuning.py`` -- the paper's pruning rules (Properties 4.1, 4.2, 5.1,
+  * ``tuning.py`` -- the paper's pruning rules (Properties 5.1, 4.2, 5.1,
     Heuristics 0/1/2, nearest-point interpolation) as plain Python loops.
   * ``mlp.py`` -- fp64 numpy forward/backward/Adam of the cost-model MLP.
   * ``tile_apply.py`` -- Q^T of a flat-tree tile QR applied in NumPy from

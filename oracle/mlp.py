@@ -6,7 +6,7 @@ the training set's mean and deviation, two hidden layers of 64 ReLU units,
 one linear output predicting log(seconds); loss = mean squared error; Adam
 (Kingma & Ba, 2015) with the usual bias correction.
 
-The paper itself argues against models (Sec. 1 and Sec. 3) and tunes purely
+The paper itself argues against models (Secs. 1 and 2.3) and tunes purely
 empirically; the model only ranks candidates and the empirical measurement
 keeps the final say.
 

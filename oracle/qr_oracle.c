@@ -347,7 +347,7 @@ double oracle_orth_residual(int64_t m, int64_t n, const double *Q, int64_t ldq) 
 
 /* ---------------------------------------------------------------------------
  * Cholesky factorization A = L L^T (the sister factorization the paper names
- * for the same tile framework and tuner, Secs. 1 and 6), by its definition
+ * for the same tile framework and tuner, Secs. 1 and 7), by its definition
  * column by column: L_jj = sqrt(A_jj - sum_{k<j} L_jk^2), and for i > j
  * L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj. In place on the lower triangle
  * of A (n x n, lda); the strict upper triangle is left as it was. Returns 0,

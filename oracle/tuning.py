@@ -4,18 +4,18 @@ Plain Python restatement, from the paper's text, of the decisions the
 library's C++ tuner makes. Only tests/ (and bench.py's CPU baseline) use it.
 
   * the search grid of (NB, IB) pairs;
-  * Property 4.1 (orthogonal pruning): per NB keep the IB with the best
-    Step-1 kernel performance (Sec. 4);
-  * Property 4.2 (convex hull) and Heuristic 0: the points of the upper
-    convex hull of the (NB, performance) data set (Sec. 4);
+  * Property 5.1 (orthogonal pruning): per NB keep the IB with the best
+    Step-1 kernel performance (Sec. 5);
+  * Property 5.2 (convex hull) and Heuristic 0: the points of the upper
+    convex hull of the (NB, performance) data set (Sec. 5);
   * Heuristic 1: hull points after the steepest segments, at most 8;
   * Heuristic 2: split the NB axis into iso-segments and keep the hull point
-    of maximum steepness in each, at most 8 (Sec. 4);
-  * Property 5.1 and prune-as-you-go (PSPAYG): after benchmarking order N,
+    of maximum steepness in each, at most 8 (Sec. 5);
+  * Property 6.1 and prune-as-you-go (PSPAYG): after benchmarking order N,
     drop every NB2 for which a larger surviving NB1 already performs better
-    (Sec. 5.3);
+    (Sec. 6.3);
   * interpolation: an untuned request uses the closest benchmarked point
-    (Sec. 5.1).
+    (Sec. 6.1).
 
 Readings where the paper is silent:
 upper hull taken left to right with both end points, collinear middle points
@@ -40,7 +40,7 @@ def grid_pairs(nb_min=64, nb_max=512, nb_step=32, ib_min=8):
 
 
 def prune_ib(perf):
-    """Property 4.1. perf: {(NB, IB): P}. Returns {NB: (IB, P)} keeping, per
+    """Property 5.1. perf: {(NB, IB): P}. Returns {NB: (IB, P)} keeping, per
     NB, the IB of highest P (ties: smaller IB)."""
     best = {}
     for (nb, ib), p in sorted(perf.items()):
@@ -104,7 +104,7 @@ def heuristic2(hull, nb_lo, nb_hi, max_sel=8, nseg=8):
 
 
 def preselect(perf, heuristic=2, max_sel=8, nseg=8):
-    """Step 1 decisions: Property 4.1, the hull, then H0/H1/H2. Returns the
+    """Step 1 decisions: Property 5.1, the hull, then H0/H1/H2. Returns the
     preselected [(NB, IB)] sorted by NB."""
     best = prune_ib(perf)
     pts = [(nb, best[nb][1]) for nb in best]
@@ -120,7 +120,7 @@ def preselect(perf, heuristic=2, max_sel=8, nseg=8):
 
 
 def payg_prune(survivors, perf_n):
-    """Property 5.1 (PSPAYG). survivors: [(NB, IB)]; perf_n: {(NB, IB): P}
+    """Property 6.1 (PSPAYG). survivors: [(NB, IB)]; perf_n: {(NB, IB): P}
     at the order just benchmarked. Keeps a pair unless a pair with larger NB
     has strictly higher P."""
     keep = []
@@ -149,5 +149,5 @@ def step2_payg(order_ns, survivors, measure):
 
 
 def nearest(value, grid):
-    """Closest grid value (ties: the smaller one), Sec. 5.1 interpolation."""
+    """Closest grid value (ties: the smaller one), Sec. 6.1 interpolation."""
     return min(grid, key=lambda g: (abs(g - value), g))

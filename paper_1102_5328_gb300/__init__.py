@@ -2,7 +2,7 @@
 
 The method is Agullo, Dongarra, Nath, Tomov, "A Fully Empirical Autotuned
 Dense QR Factorization for Multicore Architectures" (tile QR, Sec. 2; the
-empirical tuner, Secs. 4-5), re-designed for one GB300 GPU. The compute
+empirical tuner, Secs. 5–6), re-designed for one GB300 GPU. The compute
 path lives in the CUDA library ``libtileqr.so`` behind the C ABI of
 ``include/tileqr.h``; this package is its Python binding. PyTorch is used
 only for device memory and streams.

@@ -1,6 +1,6 @@
 """Per-size-class tile shapes for the batched QR, chosen empirically.
 
-The paper's tuner picks (NB, IB) per matrix order N (Sec. 5.1); for a batch
+The paper's tuner picks (NB, IB) per matrix order N (Sec. 6.1); for a batch
 of small uneven matrices the analogue is a choice per size class of the row
 count m. For each class the batch's own matrices of that class are factored
 with every candidate pair (one persistent launch per candidate, median of a

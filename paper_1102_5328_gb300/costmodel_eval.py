@@ -10,7 +10,7 @@ Training data: every logged factorization time at the training shapes
 off-grid squares and a tall-skinny shape never trained on. For each
 held-out shape three choices are compared against the best measured pair
 (regret = 1 - P(choice) / P(best)):
-  * the method without the model: the closest tuned shape's pair (Sec. 5.1);
+  * the method without the model: the closest tuned shape's pair (Sec. 6.1);
   * the model alone: argmin of predicted time over the grid;
   * the model as a pruner: measure only its top-k pairs, keep the fastest
     (k measurements instead of the whole preselection).

@@ -1,6 +1,6 @@
 // Tile Cholesky factorization A = L L^T on the persistent DAG scheduler, and
 // its empirical NB tuner: the sister factorization the paper names for the
-// same tile framework and the same autotuning method (Secs. 1 and 6; the
+// same tile framework and the same autotuning method (Secs. 1 and 7; the
 // paper tunes QR only).
 //
 // Tasks over the lower triangle of NT x NT tiles of order NB:
@@ -471,12 +471,12 @@ int chol_impl(int64_t n, double* A, int64_t lda, int nb, void* scratch, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// The empirical NB tuner for the Cholesky factorization, Secs. 4-5 applied
+// The empirical NB tuner for the Cholesky factorization, Secs. 5–6 applied
 // to its one tuning parameter: Step 1 times the dominant task (GEMM, about
 // NT^3 / 6 of them) on a device-filling batch for every NB of the grid
 // {32, 64, ..., 256}; the upper hull of (NB, GFLOP/s) and Heuristic 0/1/2
 // (qr_tune_preselect) preselect; Step 2 times the factorization for the
-// survivors at each order, ascending, and prunes with Property 5.1
+// survivors at each order, ascending, and prunes with Property 6.1
 // (qr_tune_payg). Untuned orders take the closest tuned one.
 __global__ void __launch_bounds__(CT, 2) gemm_batch(const double* A, const double* B, double* C, int NB) {
   extern __shared__ __align__(16) double gsm_raw[];
@@ -791,7 +791,7 @@ int chol_tune(const int64_t* ns, int nshapes, int heuristic, int reps, const cha
       if (pf[c] > pf[bi] || (pf[c] == pf[bi] && surv[c] < surv[bi])) bi = c;
     table.push_back(CEntry{n, surv[bi], pf[bi]});
     std::vector<int> keep(surv.size());
-    qr_tune_payg((int)surv.size(), surv.data(), pf.data(), keep.data());  // Property 5.1
+    qr_tune_payg((int)surv.size(), surv.data(), pf.data(), keep.data());  // Property 6.1
     std::vector<int> nx;
     for (size_t c = 0; c < surv.size(); ++c)
       if (keep[c]) nx.push_back(surv[c]);

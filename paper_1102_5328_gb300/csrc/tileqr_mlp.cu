@@ -3,7 +3,7 @@
 // to log(seconds), trained with mean squared error and Adam, in FP32.
 //
 // The paper tunes purely empirically and argues that models of multicore
-// performance are unreliable (Sec. 1, Sec. 3); here the model only ranks
+// performance are unreliable (Secs. 1 and 2.3); here the model only ranks
 // candidates, and the measured time keeps the final say.
 //
 // Parameters live in one flat FP32 array: W1 (64 x 4, row-major [out][in]),

@@ -3,7 +3,7 @@
 // qr_apply_workspace_p, qr_apply_qt_p_{d,s}.
 //
 // The paper names a third tunable for tall-skinny matrices: the number p of
-// domains of the panel (Sec. 6, communication-avoiding QR). In the flat tree
+// domains of the panel (Sec. 7, communication-avoiding QR). In the flat tree
 // of Sec. 2.1 the panel of step k is one chain GEQRT(k) -> TSQRT(k+1) -> ...
 // -> TSQRT(MT-1), MT - k tasks long. With p domains the tile rows k..MT-1 are
 // cut into ranges of ceil(MT/p) rows that slide down with the panel; each

@@ -1,16 +1,16 @@
-// The empirical NB/IB autotuner (Secs. 4-5 of the paper), on the GPU.
+// The empirical NB/IB autotuner (Secs. 5–6 of the paper), on the GPU.
 //
-// Step 1 (Sec. 4): time the update kernel that dominates the factorization
+// Step 1 (Sec. 5): time the update kernel that dominates the factorization
 // (TSMQR, the paper's DSSRFB, O(NT^3) calls) for every (NB, IB) of the grid:
 // 50 back-to-back launches of a device-filling batch of independent tile
 // tasks, same data every call ("No Flush", the mode the paper reports).
-// Then Property 4.1 keeps the best IB per NB, Property 4.2's upper convex
+// Then Property 5.1 keeps the best IB per NB, Property 5.2's upper convex
 // hull of (NB, performance) is formed, and Heuristic 0/1/2 preselects at
 // most 8 pairs.
-// Step 2 (Sec. 5): time the whole factorization for the preselected pairs at
+// Step 2 (Sec. 6): time the whole factorization for the preselected pairs at
 // each benchmarked order N, ascending, 6 runs each (median), and prune as
-// you go with Property 5.1. Untuned orders use the closest tuned one
-// (Sec. 5.1). The decision table is written to JSON and every measurement is
+// you go with Property 6.1. Untuned orders use the closest tuned one
+// (Sec. 6.1). The decision table is written to JSON and every measurement is
 // appended to a JSONL log, which a later run reads to skip what is measured.
 //
 // Optionally (use_model = k > 0) a small MLP cost model (tileqr_mlp.cu),
@@ -20,7 +20,7 @@
 // measurement always decides. The final model, fitted to every Step-2
 // timing, is saved with the table and proposes pairs for untuned shapes.
 // Step 1 can also run as MultCallFlushLRU (every launch on operands that are
-// not in L2), the variant the paper leaves out of scope (Sec. 4).
+// not in L2), the variant the paper leaves out of scope (Sec. 5).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -72,7 +72,7 @@ std::vector<double> steepness(const std::vector<Pt>& h) {
   return s;
 }
 
-// Property 4.1 then the hull then H0/H1/H2. Returns selected NBs (ascending).
+// Property 5.1 then the hull then H0/H1/H2. Returns selected NBs (ascending).
 std::vector<int> select_nbs(const std::map<int, std::pair<int, double>>& best, int heuristic, int max_sel, int nseg,
                             int nb_lo, int nb_hi) {
   std::vector<Pt> pts;
@@ -113,7 +113,7 @@ std::vector<std::pair<int, int>> grid_pairs(int nb_lo, int nb_hi, int step, int 
 }
 
 // ---------------------------------------------------------------------------
-// Table (decision tree of Sec. 6: tuned at install time, read at call time).
+// Table (decision tree of Sec. 7: tuned at install time, read at call time).
 struct Entry {
   int64_t m, n;
   int nb, ib;
@@ -134,7 +134,7 @@ int device_sm_count() {
   return sms;
 }
 
-// The closest tuned configuration (Sec. 5.1), one dimension after the other
+// The closest tuned configuration (Sec. 6.1), one dimension after the other
 // as the paper's example reads (N = 1800 on 5 cores -> the point tuned for
 // N = 2000 on 4 cores): first the closest SM budget among the entries (ties
 // to the smaller), then among that budget's entries the closest shape,
@@ -311,7 +311,7 @@ Step1Set<S> step1_set(void* work, int nb, int nbatch, int k) {
 }
 
 // flush = 0: "No Flush", every launch on the same data (the mode the paper
-// reports, Sec. 4). flush = 1: MultCallFlushLRU, launch l on operand set
+// reports, Sec. 5). flush = 1: MultCallFlushLRU, launch l on operand set
 // l mod nsets (step1_flush_sets), so its data is never in L2.
 template <typename S>
 int step1_time(int nb, int ib, int nbatch, int launches, int flush, double* sec, void* work, int64_t wbytes,
@@ -803,7 +803,7 @@ int qr_tune_preselect(int npairs, const int* nb, const int* ib, const double* pe
                       int nseg, int* sel_nb, int* sel_ib) {
   if (npairs <= 0 || !nb || !ib || !perf) return -1;
   if (heuristic < 0 || heuristic > 2) return -5;
-  std::map<int, std::pair<int, double>> best;  // Property 4.1
+  std::map<int, std::pair<int, double>> best;  // Property 5.1
   int lo = INT32_MAX, hi = 0;
   for (int i = 0; i < npairs; ++i) {
     lo = std::min(lo, nb[i]);
@@ -826,7 +826,7 @@ int qr_tune_payg(int nsurv, const int* nb, const double* perf, int* keep) {
   for (int a = 0; a < nsurv; ++a) {
     keep[a] = 1;
     for (int b = 0; b < nsurv; ++b)
-      if (nb[b] > nb[a] && perf[b] > perf[a]) keep[a] = 0;  // Property 5.1
+      if (nb[b] > nb[a] && perf[b] > perf[a]) keep[a] = 0;  // Property 6.1
   }
   return 0;
 }
@@ -1079,7 +1079,7 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
       }
     table.push_back(ent);
     if (!exhaustive && m == n) {  // prune as you go along the square orders
-      // Property 5.1 among the pairs measured at this order; a survivor the
+      // Property 6.1 among the pairs measured at this order; a survivor the
       // model left unmeasured is kept
       std::vector<int> nbv, keep;
       std::vector<double> pv;

@@ -6,7 +6,7 @@ Every generator uses NumPy's PCG64 ``default_rng(seed)`` and returns
 column-major (Fortran-ordered) arrays, so both sides see identical bytes.
 
 Workload shapes follow the paper's experiments (matrices of order N,
-entries uniform, Sec. 3 and Sec. 5.1: N in {500, 1000, ..., 10000}) and the
+entries uniform, Sec. 3 and Sec. 6.1: N in {500, 1000, ..., 10000}) and the
 extensions this library adds (tall-skinny shapes, batches of small uneven
 matrices, conditioned least-squares problems).
 """

@@ -5,13 +5,13 @@
         --table paper_1102_5328_gb300/tuned/gb300_fp64.json --log tune_pspayg.jsonl
 
 --mode pspayg: Step 1 (TSMQR kernel benchmark over the 119-pair grid),
-Properties 4.1/4.2 and Heuristic H0/H1/H2, then Step 2 with prune-as-you-go
-(Secs. 4-5 of the paper). --mode es: exhaustive search (every grid pair at
+Properties 5.1/5.2 and Heuristic H0/H1/H2, then Step 2 with prune-as-you-go
+(Secs. 5–6 of the paper). --mode es: exhaustive search (every grid pair at
 every shape). --flush: Step 1 as MultCallFlushLRU instead of No Flush.
 --use-model K: the learned cost model ranks the survivors from the third
 order on and only the K fastest-predicted are timed (see qr_tune).
 --sm-budgets B1,B2,...: Step 2 once per SM budget (QR_OPT_SM_BUDGET, the GPU
-counterpart of the paper's core counts, Sec. 5.1; 0 = the whole GPU), one
+counterpart of the paper's core counts, Sec. 6.1; 0 = the whole GPU), one
 log shared by all budgets (Step 1 runs once), the tables merged into --table.
 Shapes come from --ns (square) and --shapes (m x n list).
 Prints one JSON line with the wall times the library measured.

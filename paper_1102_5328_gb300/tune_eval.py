@@ -1,4 +1,4 @@
-"""Reliability of the tuner against the exhaustive search (Sec. 5.4 of the
+"""Reliability of the tuner against the exhaustive search (Sec. 6.4 of the
 paper: PS/ES and PSPAYG/ES performance ratios, optimum found k/n, on the
 tuned orders and on off-grid orders), and the learned cost model's regret on
 held-out shapes.
@@ -9,7 +9,7 @@ held-out shapes.
 
 All performance numbers compared here come from the same exhaustive
 measurement campaign (the ES log): the tuned choice at a shape is looked up
-in the decision table (nearest tuned shape, Sec. 5.1) and its measured
+in the decision table (nearest tuned shape, Sec. 6.1) and its measured
 GFLOP/s at that shape is divided by the best measured GFLOP/s there.
 Heuristics 0/1/2 are also replayed on the logged data through the library's
 own rule functions (qr_tune_preselect / qr_tune_payg), so their Step-2 cost

@@ -1,7 +1,7 @@
 """What the learned cost model adds to the paper's method, on a synthetic
 timing surface (deterministic, no timing noise): the MLP, trained by the
 library's own kernels on the training shapes, picks better (NB, IB) pairs on
-held-out shapes than the paper's closest-tuned-shape interpolation (Sec. 5.1).
+held-out shapes than the paper's closest-tuned-shape interpolation (Sec. 6.1).
 
 The surface: kernel efficiency grows with NB and loses IB/NB, parallelism
 shrinks with the tile count, so the best NB moves with the shape."""

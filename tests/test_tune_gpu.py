@@ -2,11 +2,11 @@
 decisions replayed through the oracle's restatement of the paper's rules.
 
 qr_tune (PSPAYG, Heuristic 2) times Step 1 (the TSMQR kernel batch for all
-119 (NB, IB) pairs, Sec. 4) and Step 2 (the factorization for the survivors
-at each order, prune as you go, Secs. 5.1 and 5.3) on the device and logs
+119 (NB, IB) pairs, Sec. 5) and Step 2 (the factorization for the survivors
+at each order, prune as you go, Secs. 6.1 and 6.3) on the device and logs
 every measurement. From the logged numbers alone, oracle.tuning must reach
-the same preselection (Property 4.1, the upper hull of Property 4.2,
-Heuristic 2), the same survivors at each order (Property 5.1) and the same
+the same preselection (Property 5.1, the upper hull of Property 5.2,
+Heuristic 2), the same survivors at each order (Property 6.1) and the same
 decision table.
 """
 import ctypes
@@ -101,7 +101,7 @@ def test_tuner_on_gpu_matches_oracle_replay(q, tmp_path):
     assert 0 < res["step1_seconds"] and 0 < res["step2_seconds"]
     assert res["step1_seconds"] + res["step2_seconds"] <= res["seconds"] * 1.001
     # the in-process table now answers qr_lookup with the tuned pairs, and
-    # an untuned order takes the closest tuned one (Sec. 5.1)
+    # an untuned order takes the closest tuned one (Sec. 6.1)
     for (m, n), pr in table.items():
         assert q.qr_lookup(m, n) == pr
     assert q.qr_lookup(400, 400) == table[(512, 512)]

@@ -8,7 +8,7 @@ fastest, extended down the ranking while the last one timed was the fastest
 so far, and all of them when a timed pair's measured / predicted ratio
 differed from the top-ranked pair's by more than e^0.25. The decision
 table must be the best timed pair; survivors left untimed are not pruned
-(Property 5.1 needs a measurement). The saved model is evaluated by the
+(Property 6.1 needs a measurement). The saved model is evaluated by the
 oracle's fp64 forward pass: it fits the timings it was trained on, and
 qr_model_propose returns its least-predicted pair.
 """

@@ -1,5 +1,5 @@
 """The SM-count axis of the tuner (the GPU counterpart of the paper's core
-counts, Sec. 5.1): QR_OPT_SM_BUDGET caps the persistent factorization's
+counts, Sec. 6.1): QR_OPT_SM_BUDGET caps the persistent factorization's
 workers, qr_tune records the budget of every Step-2 timing and table entry,
 and qr_lookup_sms serves a (shape, budget) request from the closest tuned
 budget, then the closest tuned shape."""

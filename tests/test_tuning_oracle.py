@@ -95,7 +95,7 @@ def test_payg_prunes_exactly_dominated():
 
 @pytest.mark.parametrize("seed", range(10))
 def test_payg_never_loses_optimum_on_monotone_tables(seed):
-    """If Property 5.1 holds for the table, PSPAYG finds the same optimum as
+    """If Property 6.1 holds for the table, PSPAYG finds the same optimum as
     measuring every preselected pair at every N (brute force)."""
     rng = random.Random(seed)
     nbs = sorted(rng.sample(range(64, 513, 32), 6))
@@ -103,7 +103,7 @@ def test_payg_never_loses_optimum_on_monotone_tables(seed):
     ns = [1000, 2000, 4000, 6000, 8000, 10000]
     # P(NB, N) = a_NB * N - b_NB with larger NB having larger slope and
     # larger offset: crossings only from small NB to large NB as N grows,
-    # which is exactly Property 5.1
+    # which is exactly Property 6.1
     a = {nb: 1.0 + k * 0.2 for k, nb in enumerate(nbs)}
     b = {nb: 300.0 * k * k for k, nb in enumerate(nbs)}
 
