@@ -608,6 +608,18 @@ def main():
                                         "es_reps", "pspayg_reps", "model")}
         tuning = {k: v for k, v in tuning.items() if v is not None}
         tuning["source"] = "committed: paper_1102_5328_gb300/tuned/gb300_fp64_reliability.json (not this run)"
+        mpath = os.path.join(ROOT, "paper_1102_5328_gb300", "tuned", "gb300_fp64_model_eval.json")
+        if os.path.exists(mpath):
+            with open(mpath) as f:
+                mj = json.load(f)
+            tuning["with_model"] = {
+                "tuning_seconds": mj["model"]["seconds"], "plain_tuning_seconds": mj["plain"]["seconds"],
+                "autotuned_over_grid_best": mj["model"]["mean_ratio"],
+                "autotuned_over_grid_best_min": mj["model"]["min_ratio"],
+                "heldout_proposal_over_grid_best": mj["model"].get("heldout_proposal_mean_ratio"),
+                "factorizations_timed": mj["model"]["factorizations_timed"],
+                "plain_factorizations_timed": mj["plain"]["factorizations_timed"],
+                "source": "committed: paper_1102_5328_gb300/tuned/gb300_fp64_model_eval.json (not this run)"}
 
     if rank == 0:
         line = {

@@ -97,3 +97,32 @@ def test_batched_graph_replay(q):
     for w, e in zip(work, eager):
         assert torch.equal(w, e)
     _check_fp64(q, plan, mats_np, work, full=False)
+
+
+def test_batched_tuned_classes_up_to_512(q):
+    """The full size range of the batched workload (m ~ U{32..512}) with the
+    tuned size classes (the committed table: for m > 256 a multi-tile class),
+    FP64 and FP32, matrix by matrix against the oracle: the classes whose
+    chunks are narrower than 32 columns take the staggered staging path."""
+    mats_np = _batch(40, seed=13, m_hi=512)
+    assert max(a.shape[0] for a in mats_np) > 256
+    outs = [_dev(a) for a in mats_np]
+    plan = q.BatchedPlan(outs, 0, 0)
+    nbs = plan.nb.tolist()
+    assert any(nb < a.shape[0] for nb, a in zip(nbs, mats_np)), nbs  # a multi-tile class
+    plan.launch()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    _check_fp64(q, plan, mats_np, outs, full=False)
+    outs32 = [_dev(a, torch.float32) for a in mats_np]
+    plan32 = q.BatchedPlan(outs32, 0, 0)
+    plan32.launch()
+    torch.cuda.synchronize()
+    for A_np, A in zip(mats_np, outs32):
+        m, n = A_np.shape
+        R = np.triu(A[:n].double().cpu().numpy())
+        F, _ = oracle.geqr2(A_np.astype(np.float32).astype(np.float64))
+        R_or = np.triu(F[:n])
+        D = oracle.row_signs(R, R_or)
+        rel = np.linalg.norm(D[:, None] * R - R_or) / np.linalg.norm(R_or)
+        assert rel <= 10 * n * U32, rel
