@@ -82,11 +82,10 @@ __device__ __forceinline__ void stx(S* p, S v, bool sm) {
 // before its first store, so a thread has U global loads in flight instead
 // of one load-store round trip per element. Element (r, c) is read only if
 // rd(r, c) (else taken as 0); f(r, c, v) gives the value stored (masks such
-// as the unit diagonal). gpad > 0 staggers the 32-row groups of each column
-// by gpad elements (row r stored at r + (r / 32) gpad).
+// as the unit diagonal).
 template <int U, typename S, typename R, typename F>
 __device__ __forceinline__ void stage_block(S* dst, int ldd, const S* src, int64_t lds, int rows, int cols, R rd,
-                                            F f, int gpad = 0) {
+                                            F f) {
   const int total = rows * cols;
   for (int base = threadIdx.x; base < total; base += U * NTHREADS) {
     S v[U];
@@ -104,7 +103,7 @@ __device__ __forceinline__ void stage_block(S* dst, int ldd, const S* src, int64
       const int idx = base + u * NTHREADS;
       if (idx < total) {
         const int c = idx / rows, r = idx - c * rows;
-        dst[r + (r >> 5) * gpad + (size_t)c * ldd] = f(r, c, v[u]);
+        dst[r + (size_t)c * ldd] = f(r, c, v[u]);
       }
     }
   }
@@ -142,18 +141,16 @@ __device__ __forceinline__ S cta_sum(S v, S* red) {
 }
 
 // Reflectors pc0 .. pc0+pb-1 of a tile V (ld ldv), rows r0 .. r0+nr-1, into
-// buf (reflector stride nrs; row rl of a reflector at rl + (rl / 32) gpad,
-// so consecutive 32-row groups are gpad elements apart) with their masks (GE:
-// zero above the diagonal, unit diagonal; TS tri: zero below it); zero past
-// `rows`. GE: four loads in flight per
+// buf (ld nr) with their masks (GE: zero above the diagonal, unit diagonal;
+// TS tri: zero below it); zero past `rows`. GE: four loads in flight per
 // thread. TS: one (its later blocks come through the cp.async prefetch of
 // apply_qt, and the TS update keeps more registers live).
 // TS with use_async (no triangle mask, V and ldv 16-byte aligned): 16-byte
 // cp.async copies, zero-filled past `rows`, all in flight at once; the
 // caller issues cp.async.wait_all before the barrier that publishes them.
 template <typename S, bool TS>
-__device__ __forceinline__ void stage_refl(S* buf, const S* V, int ldv, int nr, int nrs, int gpad, int r0, int rows,
-                                           int pc0, int pb, bool tri, bool use_async = false) {
+__device__ __forceinline__ void stage_refl(S* buf, const S* V, int ldv, int nr, int r0, int rows, int pc0, int pb,
+                                           bool tri, bool use_async = false) {
   if constexpr (TS) {
     if (use_async) {
       constexpr int EPC = 16 / sizeof(S);
@@ -162,7 +159,7 @@ __device__ __forceinline__ void stage_refl(S* buf, const S* V, int ldv, int nr, 
         const int p = idx / half, rl = EPC * (idx - (idx / half) * half), r = rl + r0;
         const int valid = r < rows ? min(EPC, rows - r) * (int)sizeof(S) : 0;
         const S* src = V + (valid ? r + (size_t)(pc0 + p) * ldv : 0);
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + p * nrs + rl + (rl >> 5) * gpad);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + p * nr + rl);
         const size_t gsrc = __cvta_generic_to_global(src);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gsrc), "r"(valid) : "memory");
       }
@@ -174,12 +171,12 @@ __device__ __forceinline__ void stage_refl(S* buf, const S* V, int ldv, int nr, 
       const int r = rl + r0, pc = pc0 + p;
       S v = S(0);
       if (r < rows) v = (tri && r > pc) ? S(0) : ldg(V + r + (size_t)pc * ldv);
-      buf[p * nrs + rl + (rl >> 5) * gpad] = v;
+      buf[p * nr + rl] = v;
     }
   } else {
-    stage_block<4>(buf, nrs, V + r0 + (size_t)pc0 * ldv, ldv, nr, pb,
+    stage_block<4>(buf, nr, V + r0 + (size_t)pc0 * ldv, ldv, nr, pb,
                    [=](int rl, int p) { return rl + r0 < rows && rl + r0 > pc0 + p; },
-                   [=](int rl, int p, S v) { return rl + r0 == pc0 + p ? S(1) : v; }, gpad);
+                   [=](int rl, int p, S v) { return rl + r0 == pc0 + p ? S(1) : v; });
   }
 }
 
@@ -207,7 +204,7 @@ __device__ __forceinline__ void stage_refl(S* buf, const S* V, int ldv, int nr, 
 // tri (TS mode only): the bottom reflectors are upper triangular -- the
 // triangle-on-triangle case of a tree reduction (TTQRT/TTMQR): V(r, c) is
 // taken as zero for r > c, whatever the tile holds there.
-template <typename S, bool TS, bool TR = true, bool STG = false>
+template <typename S, bool TS, bool TR = true>
 __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, bool t_smem,
                          int lstart, int lend, int IB, S* Ctop, int ldct, S* C, int ldc, int rows,
                          int c0, int c1, const Smem<S>& sm, bool tri = false) {
@@ -231,12 +228,6 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
     const int cw = min(per, c1 - cs);
     const int g = tid / cw, c = tid - (tid / cw) * cw;
     const bool act = g < G;
-    // STG: a chunk narrower than a multiple of 32 columns puts two row
-    // groups in one warp, whose reads of the staged reflectors would fall 32
-    // elements apart, in one bank: stagger the groups by 16 bytes then (the
-    // batched kernel's small matrices; other callers compile it out)
-    const int gpad = (STG && (cw & 31)) ? EPC : 0;
-    const int gst = RPT + gpad;  // staged stride of a row group
     S creg[RPT];
 #pragma unroll
     for (int rr = 0; rr < RPT; ++rr) {
@@ -257,11 +248,10 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
       // the row groups below take no part in it
       const int ghi = (TS && tri) ? min(G, (min(rows, l0 + ib) + RPT - 1) / RPT) : G;
       const int nr = ghi * RPT - rlo_al;  // staged rows, zero-padded past `rows`
-      const int nrs = (nr / RPT) * gst;   // staged stride of a reflector
       S* vbuf = vcur ? sm.part : sm.vs;
       S* pbuf = vcur ? sm.vs : sm.part;
       const int vcap = vcur ? PART_CAP : VS_CAP;
-      int PB = vcap / nrs;
+      int PB = vcap / nr;
       if (PB > ib) PB = ib;
       if (PB < 1) PB = 1;
       const bool myrows = act && g >= glo && g < ghi;
@@ -273,7 +263,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         const int pb = min(PB, ib - pp0);
         if (!staged) {
           __syncthreads();
-          stage_refl<S, TS>(vbuf, V, ldv, nr, nrs, gpad, rlo_al, rows, l0 + pp0, pb, tri, can_pipe);
+          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri, can_pipe);
           if (pp0 == 0 && t_in_ts)
             for (int idx = tid; idx < ib * ib; idx += NTHREADS) {
               const int p = idx / ib, q = idx - (idx / ib) * ib;
@@ -288,7 +278,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
             S acc[PG];
 #pragma unroll
             for (int q = 0; q < PG; ++q) acc[q] = S(0);
-            const S* vrow = vbuf + (size_t)pg0 * nrs + (g - glo) * gst;
+            const S* vrow = vbuf + (size_t)pg0 * nr + (g * RPT - rlo_al);
             if constexpr (sizeof(S) == 4) {
               // FP32: 16-byte shared loads (4 rows of a reflector) feed 4
               // FMAs each; vbuf, nr and the row offset are multiples of 4
@@ -298,7 +288,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
 #pragma unroll
                 for (int q = 0; q < PG; ++q)
                   if (q < pgc) {
-                    const float4 v = *reinterpret_cast<const float4*>(vrow + q * nrs + r4);
+                    const float4 v = *reinterpret_cast<const float4*>(vrow + q * nr + r4);
                     acc[q] = fma(v.x, creg[r4], acc[q]);
                     acc[q] = fma(v.y, creg[r4 + 1], acc[q]);
                     acc[q] = fma(v.z, creg[r4 + 2], acc[q]);
@@ -311,7 +301,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
                 const S cv = creg[rr];
 #pragma unroll
                 for (int q = 0; q < PG; ++q)
-                  if (q < pgc) acc[q] = fma(vrow[q * nrs + rr], cv, acc[q]);
+                  if (q < pgc) acc[q] = fma(vrow[q * nr + rr], cv, acc[q]);
               }
             }
 #pragma unroll
@@ -388,7 +378,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         l0n = lstart + (TR ? bi + 1 : nblk - 2 - bi) * IB;
         ibn = min(IB, lend - l0n);
         const int ocap = vcur ? VS_CAP : PART_CAP;
-        if (ibn * nrs <= ocap && (t_smem || ibn * ibn <= NTHREADS)) {  // one T element per thread
+        if (ibn * nr <= ocap && (t_smem || ibn * ibn <= NTHREADS)) {  // one T element per thread
           pre = true;
           S* nbuf = vcur ? sm.vs : sm.part;
           const int half = nr / EPC;  // nr is a multiple of 32, so of EPC
@@ -396,7 +386,7 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
             const int p = idx / half, r = EPC * (idx - (idx / half) * half);
             const int valid = r < rows ? min(EPC, rows - r) * (int)sizeof(S) : 0;
             const S* src = V + (valid ? r + (size_t)(l0n + p) * ldv : 0);
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(nbuf + p * nrs + r + (r >> 5) * gpad);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(nbuf + p * nr + r);
             const size_t gsrc = __cvta_generic_to_global(src);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gsrc), "r"(valid) : "memory");
           }
@@ -412,15 +402,15 @@ __device__ void apply_qt(const S* __restrict__ V, int ldv, const S* T, int ldt, 
         const int pb = min(PB, ib - pp0);
         if (PB < ib) {
           __syncthreads();
-          stage_refl<S, TS>(vbuf, V, ldv, nr, nrs, gpad, rlo_al, rows, l0 + pp0, pb, tri, can_pipe);
+          stage_refl<S, TS>(vbuf, V, ldv, nr, rlo_al, rows, l0 + pp0, pb, tri, can_pipe);
           asm volatile("cp.async.wait_all;" ::: "memory");
           __syncthreads();
         }
         if (myrows) {
-          const S* vrow = vbuf + (g - glo) * gst;
+          const S* vrow = vbuf + (g * RPT - rlo_al);
           for (int p = 0; p < pb; ++p) {
             const S wv = sm.w[(pp0 + p) * cw + c];
-            const S* vp = vrow + (size_t)p * nrs;
+            const S* vp = vrow + (size_t)p * nr;
             if constexpr (sizeof(S) == 4) {
 #pragma unroll
               for (int r4 = 0; r4 < RPT; r4 += 4) {
@@ -766,7 +756,7 @@ __device__ void panel_l2(S* P, int ldp, int nr, int w, S* Rs, int ldr, S* tau, S
 // sub-panels that fit shared memory (a sub-panel is applied to the rest of
 // its block with its own temporary T), then T_l is formed and the block is
 // applied to the tile's trailing columns.
-template <typename S, bool STG = false>
+template <typename S>
 __device__ void geqrt(S* A, int lda, int rows, int cols, int IB, S* T, const Smem<S>& sm, int* bad) {
   for (int l0 = 0; l0 < cols; l0 += IB) {
     const int ib = min(IB, cols - l0);
@@ -795,7 +785,7 @@ __device__ void geqrt(S* A, int lda, int rows, int cols, int IB, S* T, const Sme
       __syncthreads();
       if (!whole && s0 + w < l0 + ib) {
         // apply the sub-panel to the rest of the block (columns s0+w .. l0+ib)
-        apply_qt<S, false, true, STG>(A, lda, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, nullptr, 0, A, lda,
+        apply_qt<S, false>(A, lda, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, nullptr, 0, A, lda,
                            rows, s0 + w, l0 + ib, sm);
       }
     }
@@ -806,7 +796,7 @@ __device__ void geqrt(S* A, int lda, int rows, int cols, int IB, S* T, const Sme
     }
     __syncthreads();
     if (l0 + ib < cols)
-      apply_qt<S, false, true, STG>(A, lda, T, IB, false, l0, l0 + ib, IB, nullptr, 0, A, lda, rows, l0 + ib, cols, sm);
+      apply_qt<S, false>(A, lda, T, IB, false, l0, l0 + ib, IB, nullptr, 0, A, lda, rows, l0 + ib, cols, sm);
     __syncthreads();
   }
 }
@@ -819,7 +809,7 @@ __device__ void geqrt(S* A, int lda, int rows, int cols, int IB, S* T, const Sme
 // B's upper triangle is another R factor (its strict lower part belongs to
 // someone else and is neither read nor written); the reflectors then live in
 // B's upper triangle, column c having rows 0..c.
-template <typename S, bool STG = false>
+template <typename S>
 __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, S* T, const Smem<S>& sm,
                       int* bad, bool tri = false) {
   for (int l0 = 0; l0 < cols; l0 += IB) {
@@ -853,7 +843,7 @@ __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, 
       }
       __syncthreads();
       if (!whole && s0 + w < l0 + ib) {
-        apply_qt<S, true, true, STG>(B, ldb, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, R, ldr, B, ldb, nr, s0 + w,
+        apply_qt<S, true>(B, ldb, sm.ts - (size_t)s0 * w, w, true, s0, s0 + w, w, R, ldr, B, ldb, nr, s0 + w,
                           l0 + ib, sm, tri);
       }
     }
@@ -865,7 +855,7 @@ __device__ void tsqrt(S* R, int ldr, S* B, int ldb, int rows, int cols, int IB, 
     }
     __syncthreads();
     if (l0 + ib < cols)
-      apply_qt<S, true, true, STG>(B, ldb, T, IB, false, l0, l0 + ib, IB, R, ldr, B, ldb, nrb, l0 + ib, cols, sm, tri);
+      apply_qt<S, true>(B, ldb, T, IB, false, l0, l0 + ib, IB, R, ldr, B, ldb, nrb, l0 + ib, cols, sm, tri);
     __syncthreads();
   }
 }
@@ -880,7 +870,7 @@ namespace tqr {
 // nref reflectors, T IB x nref), columns [c0, c1) of C. tc (FP32 tiles
 // only): TC_TF32 / TC_BF16X3 run the products on the tensor cores
 // (apply_qt_mma), TC_NONE on the FP32/FP64 cores.
-template <typename S, bool STG = false>
+template <typename S>
 __device__ void unmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C, int ldc, int c0,
                       int c1, const Smem<S>& sm, int tc = TC_NONE) {
   if constexpr (sizeof(S) == 4) {
@@ -893,7 +883,7 @@ __device__ void unmqr(const S* V, int ldv, const S* T, int IB, int rows, int nre
          apply_qt_mma<TC_BF16X3, false>(V, ldv, T, IB, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm.vs)))
       return;
   }
-  apply_qt<S, false, true, STG>(V, ldv, T, IB, false, 0, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm);
+  apply_qt<S, false>(V, ldv, T, IB, false, 0, nref, IB, nullptr, 0, C, ldc, rows, c0, c1, sm);
 }
 
 // TSMQR: [C1; C2] <- Q^T [C1; C2] for the TSQRT factors (V rows x nref in
@@ -901,7 +891,7 @@ __device__ void unmqr(const S* V, int ldv, const S* T, int IB, int rows, int nre
 // tri = true is TTMQR: V holds triangle-on-triangle reflectors (upper
 // triangular), so only the first min(rows, nref) rows of C2 change (always
 // on the FP32/FP64 cores). tc as for unmqr.
-template <typename S, bool STG = false>
+template <typename S>
 __device__ void tsmqr(const S* V, int ldv, const S* T, int IB, int rows, int nref, S* C1, int ldc1, S* C2,
                       int ldc2, int c0, int c1, const Smem<S>& sm, bool tri = false, int tc = TC_NONE) {
   if constexpr (sizeof(S) == 4) {
@@ -914,7 +904,7 @@ __device__ void tsmqr(const S* V, int ldv, const S* T, int IB, int rows, int nre
          apply_qt_mma<TC_BF16X3, true>(V, ldv, T, IB, nref, IB, C1, ldc1, C2, ldc2, rows, c0, c1, sm.vs)))
       return;
   }
-  apply_qt<S, true, true, STG>(V, ldv, T, IB, false, 0, nref, IB, C1, ldc1, C2, ldc2, tri ? min(rows, nref) : rows, c0, c1,
+  apply_qt<S, true>(V, ldv, T, IB, false, 0, nref, IB, C1, ldc1, C2, ldc2, tri ? min(rows, nref) : rows, c0, c1,
                     sm, tri);
 }
 

@@ -67,17 +67,17 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     auto rows = [&](int i) { return min(NB, m - i * NB); };
     auto cols = [&](int j) { return min(NB, n - j * NB); };
     for (int k = 0; k < min(MT, NT); ++k) {
-      geqrt<S, true>(tile(k, k), lda, rows(k), cols(k), IB, tf(k, k), sm, status);
+      geqrt<S>(tile(k, k), lda, rows(k), cols(k), IB, tf(k, k), sm, status);
       __syncthreads();
       for (int j = k + 1; j < NT; ++j) {
-        unmqr<S, true>(tile(k, k), lda, tf(k, k), IB, rows(k), cols(k), tile(k, j), lda, 0, cols(j), sm);
+        unmqr<S>(tile(k, k), lda, tf(k, k), IB, rows(k), cols(k), tile(k, j), lda, 0, cols(j), sm);
         __syncthreads();
       }
       for (int i = k + 1; i < MT; ++i) {
-        tsqrt<S, true>(tile(k, k), lda, tile(i, k), lda, rows(i), cols(k), IB, tf(i, k), sm, status);
+        tsqrt<S>(tile(k, k), lda, tile(i, k), lda, rows(i), cols(k), IB, tf(i, k), sm, status);
         __syncthreads();
         for (int j = k + 1; j < NT; ++j) {
-          tsmqr<S, true>(tile(i, k), lda, tf(i, k), IB, rows(i), cols(k), tile(k, j), lda, tile(i, j), lda, 0, cols(j), sm);
+          tsmqr<S>(tile(i, k), lda, tf(i, k), IB, rows(i), cols(k), tile(k, j), lda, tile(i, j), lda, 0, cols(j), sm);
           __syncthreads();
         }
       }

@@ -35,13 +35,18 @@ def _factor(q, A_np, nb, ib, budget, trace=False):
     q.qr_set_option(q.QR_OPT_SM_BUDGET, budget)
     try:
         A = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()
+        # T's storage has entries the factorization never writes (below the
+        # diagonal of each IB x IB block, tiles above the diagonal): start
+        # every run from zeros so the comparison sees only what was computed
+        t_elems, _ = q.qr_workspace(A.shape[0], A.shape[1], nb, ib, A.dtype)
+        T = torch.zeros(max(t_elems, 1), dtype=A.dtype, device="cuda")
         buf = None
         if trace:
             ntasks = q.qr_task_count(A.shape[0], A.shape[1], nb, ib)
             buf = torch.full((ntasks, 4), -1, dtype=torch.int64, device="cuda")
             q.qr_set_trace(buf)
         try:
-            f = q.qr_factor(A, nb, ib)
+            f = q.qr_factor(A, nb, ib, T=T)
             torch.cuda.synchronize()
         finally:
             if trace:
