@@ -38,7 +38,8 @@ SEED = 10000
 # (profiles/persistent_qr_fp64_n10000.md), not measured by this run; None for
 # any other configuration.
 TRAFFIC_BYTES = {(10000, 10000, 128, 8): 57.57e9 + 41.40e9}
-TRAFFIC_SOURCE = "carried over: ncu capture in profiles/persistent_qr_fp64_n10000.md (same kernel sources)"
+TRAFFIC_SOURCE = ("ncu capture of this kernel and configuration (dram__bytes_read.sum + dram__bytes_write.sum, "
+                  "profiles/persistent_qr_fp64_n10000.md), not measured in this run")
 
 
 def max_over_ranks(x, device="cuda"):

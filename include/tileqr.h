@@ -65,6 +65,9 @@ extern "C" {
 #define QR_OPT_SM_BUDGET      13 /* SMs the persistent factorizations may use (0 = all): the grid is capped at that many
                                     SMs' worth of CTAs and the list schedule plans for as many workers -- the GPU
                                     counterpart of the paper's core count (Sec. 6.1); qr_tune records it per entry */
+#define QR_OPT_TUNE_IB_TOL    14 /* qr_tune Step 1, in 1/1000 (default 0 = Property 5.1 as stated: the best IB per NB
+                                    only): each preselected NB also keeps every IB whose kernel rate is within this
+                                    fraction of its best IB's, so that Step 2 decides between them */
 
 /*
  * qr_workspace -- sizes of the caller-owned buffers of qr_factor_*.

@@ -119,6 +119,22 @@ def preselect(perf, heuristic=2, max_sel=8, nseg=8):
     return [(nb, best[nb][0]) for nb in sel]
 
 
+def widen_ib(perf, pre, tol):
+    """An extension of Property 5.1 (the paper keeps only the best IB per NB;
+    tol = 0 is that rule): each preselected (NB, IB*) also brings every other
+    IB of that NB whose Step-1 rate is at least (1 - tol) times IB*'s, in
+    ascending IB after IB*, so that Step 2 decides between IBs the kernel
+    benchmark cannot tell apart. pre: preselect()'s list."""
+    out = []
+    for nb, ib0 in pre:
+        out.append((nb, ib0))
+        if tol <= 0:
+            continue
+        p0 = perf[(nb, ib0)]
+        out += [(nb, ib) for (n2, ib) in sorted(perf) if n2 == nb and ib != ib0 and perf[(nb, ib)] >= (1.0 - tol) * p0]
+    return out
+
+
 def payg_prune(survivors, perf_n):
     """Property 6.1 (PSPAYG). survivors: [(NB, IB)]; perf_n: {(NB, IB): P}
     at the order just benchmarked. Keeps a pair unless a pair with larger NB

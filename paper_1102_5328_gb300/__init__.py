@@ -38,6 +38,7 @@ QR_OPT_LS_REFINE = 10
 QR_OPT_GMRES_MAX = 11
 QR_OPT_GMRES_TOL_EXP = 12
 QR_OPT_SM_BUDGET = 13
+QR_OPT_TUNE_IB_TOL = 14
 
 
 _TUNED_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")

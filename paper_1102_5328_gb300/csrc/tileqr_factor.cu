@@ -55,6 +55,7 @@ int g_record = 0;
 int g_ls_refine = 0;     // QR_OPT_LS_REFINE
 int g_gmres_max = 50;    // QR_OPT_GMRES_MAX
 int g_gmres_tol_exp = 6;  // QR_OPT_GMRES_TOL_EXP
+int g_tune_ib_tol = 0;    // QR_OPT_TUNE_IB_TOL (1/1000)
 cudaEvent_t g_ev[2] = {nullptr, nullptr};
 bool g_ev_pending = false;
 
@@ -791,6 +792,10 @@ int qr_set_option(int opt, int64_t value) {
       if (value < 1 || value > 16) return -2;
       g_gmres_tol_exp = (int)value;
       return 0;
+    case QR_OPT_TUNE_IB_TOL:
+      if (value < 0 || value > 500) return -2;
+      g_tune_ib_tol = (int)value;
+      return 0;
   }
   return -1;
 }
@@ -811,6 +816,7 @@ int64_t qr_get_option(int opt) {
     case QR_OPT_LS_REFINE: return g_ls_refine;
     case QR_OPT_GMRES_MAX: return g_gmres_max;
     case QR_OPT_GMRES_TOL_EXP: return g_gmres_tol_exp;
+    case QR_OPT_TUNE_IB_TOL: return g_tune_ib_tol;
   }
   return INT64_MIN;
 }

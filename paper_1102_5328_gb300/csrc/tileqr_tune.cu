@@ -967,7 +967,19 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
     std::vector<int> sn(grid.size()), si(grid.size());
     const int k = qr_tune_preselect((int)grid.size(), nb.data(), ib.data(), perf.data(), heuristic, 8, 8, sn.data(),
                                     si.data());
-    for (int i = 0; i < k; ++i) cand.push_back({sn[i], si[i]});
+    // QR_OPT_TUNE_IB_TOL > 0: each preselected NB also brings every other IB
+    // whose kernel rate is within that tolerance of its best IB's (ascending
+    // IB after the best); 0 is Property 5.1 as the paper states it
+    const double tol = (double)qr_get_option(QR_OPT_TUNE_IB_TOL) / 1000.0;
+    for (int i = 0; i < k; ++i) {
+      cand.push_back({sn[i], si[i]});
+      if (tol <= 0) continue;
+      double pbest = 0;
+      for (size_t g = 0; g < grid.size(); ++g)
+        if (nb[g] == sn[i] && ib[g] == si[i]) pbest = perf[g];
+      for (size_t g = 0; g < grid.size(); ++g)
+        if (nb[g] == sn[i] && ib[g] != si[i] && perf[g] >= (1.0 - tol) * pbest) cand.push_back({nb[g], ib[g]});
+    }
   }
   // Step 2: shapes in ascending order of n (then m), PSPAYG between orders
   std::vector<int> order(nshapes);
@@ -1131,9 +1143,10 @@ int qr_tune(const int64_t* ms, const int64_t* ns, int nshapes, int heuristic, in
     snprintf(extra, sizeof(extra),
              "  \"heuristic\": %d,\n  \"mode\": \"%s\",\n  \"step1\": \"%s\",\n  \"use_model\": %d,\n"
              "  \"reps\": %d,\n  \"seconds\": %.3f,\n  \"step1_seconds\": %.3f,\n  \"step2_seconds\": %.3f,\n"
-             "  \"model_seconds\": %.3f,\n  \"factorizations_timed\": %d,\n  \"model_fallbacks\": %d,\n",
+             "  \"model_seconds\": %.3f,\n  \"factorizations_timed\": %d,\n  \"model_fallbacks\": %d,\n"
+             "  \"ib_tol_permille\": %d,\n",
              heuristic, exhaustive ? "exhaustive" : "pspayg", flush ? "multcallflushlru" : "noflush", use_model,
-             reps, total, step1_s, step2_s, model_s, measured, fallbacks);
+             reps, total, step1_s, step2_s, model_s, measured, fallbacks, (int)qr_get_option(QR_OPT_TUNE_IB_TOL));
     std::string ex = extra;
     if (final_model.ok) ex += model_json(final_model);
     if (!write_table(table_path, prec == QR_PREC_F32 ? 1 : 0, table, ex)) return -9;

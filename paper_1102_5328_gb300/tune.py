@@ -53,7 +53,17 @@ def write_table(path, tab):
         f.write("\n".join(lines) + "\n")
 
 
-def run(shapes, mode, heuristic, reps, prec, table, log, stream=None, use_model=0, flush=False):
+def run(shapes, mode, heuristic, reps, prec, table, log, stream=None, use_model=0, flush=False, ib_tol=0):
+    from . import QR_OPT_TUNE_IB_TOL, qr_get_option, qr_set_option
+    old_tol = qr_get_option(QR_OPT_TUNE_IB_TOL)
+    qr_set_option(QR_OPT_TUNE_IB_TOL, int(ib_tol))
+    try:
+        return _run(shapes, mode, heuristic, reps, prec, table, log, stream, use_model, flush, ib_tol)
+    finally:
+        qr_set_option(QR_OPT_TUNE_IB_TOL, old_tol)
+
+
+def _run(shapes, mode, heuristic, reps, prec, table, log, stream, use_model, flush, ib_tol):
     L = lib()
     max_m = max(m for m, _ in shapes)
     max_n = max(n for _, n in shapes)
@@ -74,7 +84,8 @@ def run(shapes, mode, heuristic, reps, prec, table, log, stream=None, use_model=
                    (log or "").encode(), ctypes.c_void_p(work.data_ptr()), need, secs, ctypes.c_void_p(s.cuda_stream))
     _lib.check(rc, "qr_tune")
     return {"mode": mode, "heuristic": heuristic, "reps": reps, "use_model": int(use_model),
-            "step1": "multcallflushlru" if flush else "noflush", "shapes": shapes, "seconds": secs[0],
+            "step1": "multcallflushlru" if flush else "noflush", "ib_tol_permille": int(ib_tol),
+            "shapes": shapes, "seconds": secs[0],
             "step1_seconds": secs[1], "step2_seconds": secs[2], "factorizations_timed": int(secs[3]),
             "model_seconds": secs[4], "model_fallbacks": int(secs[5]),
             "table": table, "log": log, "max_m": max_m, "max_n": max_n}
@@ -93,13 +104,16 @@ def main(argv=None):
     ap.add_argument("--use-model", type=int, default=0)
     ap.add_argument("--flush", action="store_true")
     ap.add_argument("--sm-budgets", default="", help="comma-separated SM budgets (0 = whole GPU)")
+    ap.add_argument("--ib-tol", type=int, default=0,
+                    help="Step 1: keep, per preselected NB, every IB within this many 1/1000 of its best IB's rate")
     a = ap.parse_args(argv)
     if a.table:
         os.makedirs(os.path.dirname(os.path.abspath(a.table)), exist_ok=True)
     prec = QR_PREC_F32 if a.prec == "f32" else QR_PREC_F64
     shapes = parse_shapes(a.ns, a.shapes)
     if not a.sm_budgets:
-        res = run(shapes, a.mode, a.heuristic, a.reps, prec, a.table, a.log, use_model=a.use_model, flush=a.flush)
+        res = run(shapes, a.mode, a.heuristic, a.reps, prec, a.table, a.log, use_model=a.use_model, flush=a.flush,
+                  ib_tol=a.ib_tol)
         print(json.dumps(res))
         return 0
     from . import QR_OPT_SM_BUDGET, qr_set_option
@@ -108,7 +122,8 @@ def main(argv=None):
         for b in [int(v) for v in a.sm_budgets.split(",") if v]:
             qr_set_option(QR_OPT_SM_BUDGET, b)
             tb = (a.table or "tune_table.json") + ".sms%d" % b
-            r = run(shapes, a.mode, a.heuristic, a.reps, prec, tb, a.log, use_model=a.use_model, flush=a.flush)
+            r = run(shapes, a.mode, a.heuristic, a.reps, prec, tb, a.log, use_model=a.use_model, flush=a.flush,
+                    ib_tol=a.ib_tol)
             r["sm_budget"] = b
             runs.append(r)
             t = json.load(open(tb))

@@ -88,6 +88,7 @@ def replay(heuristic, step1, es, tuned_shapes, sms=152):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--es", required=True, help="JSONL log of the exhaustive run")
+    ap.add_argument("--es-held", default="", help="JSONL log of the exhaustive run over the held-out shapes")
     ap.add_argument("--pspayg", required=True, help="JSONL log of the PSPAYG run (Step 1 data)")
     ap.add_argument("--table", required=True, help="decision table written by the PSPAYG run")
     ap.add_argument("--tune-json", default="", help="JSON line printed by the PSPAYG run")
@@ -99,6 +100,8 @@ def main(argv=None):
 
     step1, _ = load_log(a.pspayg)
     _, es = load_log(a.es)
+    if a.es_held:
+        es.update(load_log(a.es_held)[1])
     with open(a.table) as f:
         tab = json.load(f)
     decision = {(e["m"], e["n"]): (e["nb"], e["ib"]) for e in tab["entries"]}
@@ -120,8 +123,9 @@ def main(argv=None):
                      "pairs_measured_es": len(cands)})
     ratios = [r["ratio"] for r in rows]
     res = {
-        "source": "ES log %s, PSPAYG log %s, table %s" % (os.path.basename(a.es), os.path.basename(a.pspayg),
-                                                        os.path.basename(a.table)),
+        "source": "ES log %s, PSPAYG log %s, table %s" % (
+            " + ".join(os.path.basename(x) for x in (a.es, a.es_held) if x), os.path.basename(a.pspayg),
+            os.path.basename(a.table)),
         "heuristic": tab.get("heuristic"),
         "autotuned_over_grid_best": float(np.mean(ratios)),
         "autotuned_over_grid_best_min": float(np.min(ratios)),

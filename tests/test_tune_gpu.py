@@ -46,19 +46,19 @@ def _read_log(path):
         return [json.loads(line) for line in f if line.strip()]
 
 
-def run_tune(q, shapes, tmp_path, prec, reps=2, heuristic=2, mode=0, tag="t"):
+def run_tune(q, shapes, tmp_path, prec, reps=2, heuristic=2, mode=0, tag="t", ib_tol=0):
     from paper_1102_5328_gb300 import tune
     table = str(tmp_path / ("%s_table.json" % tag))
     log = str(tmp_path / ("%s_log.jsonl" % tag))
-    res = tune.run(shapes, "es" if mode else "pspayg", heuristic, reps, prec, table, log)
+    res = tune.run(shapes, "es" if mode else "pspayg", heuristic, reps, prec, table, log, ib_tol=ib_tol)
     return res, json.load(open(table)), _read_log(log)
 
 
-def replay(log, shapes, sms, heuristic=2):
+def replay(log, shapes, sms, heuristic=2, ib_tol=0.0):
     """The tuner's decisions recomputed by the oracle from its own log."""
     perf1 = {(e["nb"], e["ib"]): 2.0 * sms * 4.0 * e["nb"] ** 3 / e["seconds"] / 1e9
              for e in log if e["kind"] == 1}
-    pre = tuning.preselect(perf1, heuristic=heuristic)
+    pre = tuning.widen_ib(perf1, tuning.preselect(perf1, heuristic=heuristic), ib_tol)
     step2 = {}
     for e in log:
         if e["kind"] == 2:
@@ -117,3 +117,24 @@ def test_tuner_resumes_from_its_log(q, tmp_path):
     assert res2["factorizations_timed"] == 0 and res2["step1_seconds"] == 0
     assert len(log2) == len(log1)
     assert tab1["entries"] == tab2["entries"]
+
+
+def test_tuner_ib_tolerance_replays(q, tmp_path):
+    """QR_OPT_TUNE_IB_TOL (here 5 %): each preselected NB also brings the IBs
+    within 5 % of its best IB's Step-1 rate; Step 2 measures exactly the
+    oracle's widened survivors and the table is the oracle's decision."""
+    shapes = [(256, 256), (512, 512), (768, 768)]
+    res, tab, log = run_tune(q, shapes, tmp_path, q.QR_PREC_F64, tag="w", ib_tol=50)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    perf1, pre, measured, table = replay(log, shapes, sms, ib_tol=0.05)
+    plain = tuning.preselect(perf1, heuristic=2)
+    assert set(plain) <= set(pre)
+    got = {}
+    for e in log:
+        if e["kind"] == 2:
+            got.setdefault((e["m"], e["n"]), []).append((e["nb"], e["ib"]))
+    assert {k: sorted(v) for k, v in got.items()} == measured
+    assert measured[(256, 256)] == sorted(pre)
+    entries = {(e["m"], e["n"]): (e["nb"], e["ib"]) for e in tab["entries"]}
+    assert entries == table
+    assert tab["ib_tol_permille"] == 50 and q.qr_get_option(q.QR_OPT_TUNE_IB_TOL) == 0

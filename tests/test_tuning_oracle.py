@@ -132,3 +132,16 @@ def test_interpolation_example_from_paper():
     n, c = g["query"]
     assert (tuning.nearest(n, g["grid_N"]), tuning.nearest(c, g["grid_cores"])) == tuple(g["expect"])
     assert tuning.nearest(1500, [1000, 2000]) == 1000  # tie -> smaller
+
+
+def test_widen_ib_keeps_the_ibs_within_tolerance():
+    """The IB-tolerance extension of Property 5.1: tol = 0 is the paper's rule
+    (the best IB only); a pair enters when its rate is at least (1 - tol)
+    times the best IB's of the same NB, after that pair, ascending IB."""
+    perf = {(64, 8): 100.0, (64, 16): 101.0, (64, 32): 90.0, (128, 8): 200.0, (128, 16): 150.0}
+    pre = [(64, 16), (128, 8)]
+    assert tuning.widen_ib(perf, pre, 0.0) == pre
+    assert tuning.widen_ib(perf, pre, 0.0099) == pre  # 100 < 0.9901 * 101
+    assert tuning.widen_ib(perf, pre, 0.02) == [(64, 16), (64, 8), (128, 8)]
+    assert tuning.widen_ib(perf, pre, 0.11) == [(64, 16), (64, 8), (64, 32), (128, 8)]
+    assert tuning.widen_ib(perf, pre, 0.3) == [(64, 16), (64, 8), (64, 32), (128, 8), (128, 16)]
