@@ -605,7 +605,9 @@ def main():
             tj = json.load(f)
         tuning = {k: tj.get(k) for k in ("autotuned_over_grid_best", "autotuned_over_grid_best_min",
                                         "optimum_found", "tuning_seconds", "full_grid_seconds",
-                                        "full_grid_seconds_basis", "tuning_over_full_grid", "heuristic",
+                                        "full_grid_seconds_basis", "tuning_over_full_grid",
+                                        "tuning_seconds_tuned_orders", "tuning_over_full_grid_tuned_orders",
+                                        "tuned_orders_basis", "heuristic", "ib_tol_permille", "use_model",
                                         "es_reps", "pspayg_reps", "model")}
         tuning = {k: v for k, v in tuning.items() if v is not None}
         tuning["source"] = "committed: paper_1102_5328_gb300/tuned/gb300_fp64_reliability.json (not this run)"

@@ -145,6 +145,15 @@ def main(argv=None):
     res["full_grid_seconds"] = float(sum(6 * v[0] for k, v in es.items() if (k[0], k[1]) in tuned))
     if "tuning_seconds" in res:
         res["tuning_over_full_grid"] = res["tuning_seconds"] / res["full_grid_seconds"]
+        # the same accounting as the full grid, on the same shapes: Step 1 plus
+        # 6 x the per-point time of every Step-2 timing at the tuned orders
+        # (the measured wall time above also holds the tall-skinny shapes and
+        # their panel-domain sweeps, which the full grid does not)
+        _, own = load_log(a.pspayg)
+        sq = float(sum(6 * v[0] for k, v in own.items() if (k[0], k[1]) in tuned))
+        res["tuning_seconds_tuned_orders"] = res["tuning_step1_seconds"] + sq
+        res["tuning_over_full_grid_tuned_orders"] = res["tuning_seconds_tuned_orders"] / res["full_grid_seconds"]
+        res["factorizations_timed_tuned_orders"] = sum(1 for k in own if (k[0], k[1]) in tuned)
     # replay H0/H1/H2 on the logged data (Table 1 / Table 2 format)
     reps = {}
     for h in (0, 1, 2):

@@ -1,0 +1,78 @@
+"""The committed tuning results against the committed measurements they were
+derived from (CPU only): the decision tables follow from their own logs by
+the oracle's restatement of the rules, and the reliability figures follow
+from the logs and the exhaustive search."""
+import json
+import os
+
+import pytest
+
+from oracle import tuning
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TUNED = os.path.join(HERE, "..", "paper_1102_5328_gb300", "tuned")
+SMS = 152  # the GB300 the logs were taken on
+
+
+def _log(name):
+    with open(os.path.join(TUNED, name)) as f:
+        return [json.loads(line) for line in f if line.strip()]
+
+
+def _table(name):
+    with open(os.path.join(TUNED, name)) as f:
+        return json.load(f)
+
+
+def _flops(m, n):
+    return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+def _replay_squares(log, tol):
+    """Step 1 -> Property 5.1 (widened by tol) -> hull -> Heuristic 2, then
+    PSPAYG over the square orders on the logged Step-2 timings."""
+    perf1 = {(e["nb"], e["ib"]): 2.0 * SMS * 4.0 * e["nb"] ** 3 / e["seconds"] / 1e9 for e in log if e["kind"] == 1}
+    pre = tuning.widen_ib(perf1, tuning.preselect(perf1, heuristic=2), tol)
+    sec = {(e["m"], e["nb"], e["ib"]): e["seconds"] for e in log if e["kind"] == 2 and e["m"] == e["n"]}
+    orders = sorted({k[0] for k in sec})
+    want, count = tuning.step2_payg(orders, pre, lambda n, pr: _flops(n, n) / sec[(n,) + pr])
+    return pre, want, count
+
+
+@pytest.mark.parametrize("log,table,tol", [("gb300_fp64_h2.jsonl", "gb300_fp64_h2.json", 0.0),
+                                           ("gb300_fp64_plain.jsonl", "gb300_fp64_plain.json", 0.02)])
+def test_plain_tables_follow_from_their_logs(log, table, tol):
+    L, tab = _log(log), _table(table)
+    pre, want, count = _replay_squares(L, tol)
+    assert tab.get("ib_tol_permille", 0) == round(1000 * tol)  # tables written before the option have none
+    got = {e["m"]: (e["nb"], e["ib"]) for e in tab["entries"] if e["m"] == e["n"]}
+    assert got == {n: v[0] for n, v in want.items()}
+    assert count == sum(1 for e in L if e["kind"] == 2 and e["m"] == e["n"])
+
+
+def test_installed_table_decides_as_the_plain_search():
+    """The model-guided search (installed table) timed fewer pairs but chose
+    the same (NB, IB, p) at every shape as the search without the model."""
+    a, b = _table("gb300_fp64.json"), _table("gb300_fp64_plain.json")
+    key = lambda t: {(e["m"], e["n"]): (e["nb"], e["ib"], e["p"]) for e in t["entries"]}
+    assert key(a) == key(b)
+    assert a["use_model"] == 1 and a["ib_tol_permille"] == 20 and "model" in a
+    assert a["factorizations_timed"] < b["factorizations_timed"]
+
+
+@pytest.mark.parametrize("rel,log,table,run", [
+    ("gb300_fp64_reliability.json", "gb300_fp64_pspayg.jsonl", "gb300_fp64.json", "gb300_fp64_pspayg_run.json"),
+    ("gb300_fp64_h2_reliability.json", "gb300_fp64_h2.jsonl", "gb300_fp64_h2.json", "gb300_fp64_h2_run.json")])
+def test_reliability_reproduces(tmp_path, rel, log, table, run):
+    from paper_1102_5328_gb300 import tune_eval
+    out = str(tmp_path / "rel.json")
+    j = lambda n: os.path.join(TUNED, n)
+    assert tune_eval.main(["--es", j("gb300_fp64_es.jsonl"), "--es-held", j("gb300_fp64_es_held.jsonl"),
+                           "--pspayg", j(log), "--table", j(table), "--tune-json", j(run),
+                           "--es-json", j("gb300_fp64_es_run.json"), "--out", out]) == 0
+    got, want = json.load(open(out)), _table(rel)
+    for k in ("autotuned_over_grid_best", "autotuned_over_grid_best_min", "optimum_found", "tuning_seconds",
+              "full_grid_seconds", "tuning_seconds_tuned_orders", "factorizations_timed_tuned_orders"):
+        assert got[k] == pytest.approx(want[k], rel=1e-12), k
+    # every ratio is a grid point's time over the grid best's, from the exhaustive logs
+    assert all(0 < r["ratio"] <= 1 for r in got["per_shape"])
