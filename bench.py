@@ -292,17 +292,29 @@ def run_ls(args):
             nb, ib = args.nb, args.ib
         pd = args.ls_p if args.ls_p else pd
         tol = args.ls_tol if prec != q.QR_PREC_F64 else 2.0 ** -52
-        X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it, tol=tol, p=pd)  # warm-up
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(max(args.steps, 3)):
-            t0 = time.perf_counter()
-            X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb, ib=ib, max_iter=it, tol=tol, p=pd)
+        # the FP64 baseline: the factorization table's pair, and, when its
+        # tiles are larger than 64, NB = 64 with the same IB and the library's
+        # domain count (the few-column Q applications stage 64-row tiles
+        # whole); the faster solve is the baseline, both are reported
+        cands = [(nb, ib, pd)]
+        if prec == q.QR_PREC_F64 and not args.nb and nb > 64:
+            cands.append((64, ib, 0))
+        for ci, (nb_c, ib_c, p_c) in enumerate(cands):
+            X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb_c, ib=ib_c, max_iter=it, tol=tol, p=p_c)  # warm-up
             torch.cuda.synchronize()
-            ts.append(time.perf_counter() - t0)
-        res[name] = {"median_s": statistics.median(ts), "info": list(info), "nb": nb, "ib": ib, "p": pd, "tol": tol,
-                     "refine": ["none", "augmented", "gmres"][refine] if prec != q.QR_PREC_F64 else "none",
-                     "X": X.cpu().numpy()}
+            ts = []
+            for _ in range(max(args.steps, 3)):
+                t0 = time.perf_counter()
+                X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb_c, ib=ib_c, max_iter=it, tol=tol, p=p_c)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            r = {"median_s": statistics.median(ts), "info": list(info), "nb": nb_c, "ib": ib_c, "p": p_c, "tol": tol,
+                 "refine": ["none", "augmented", "gmres"][refine] if prec != q.QR_PREC_F64 else "none",
+                 "X": X.cpu().numpy()}
+            if len(cands) > 1:
+                res["%s_%s" % (name, "table_pair" if ci == 0 else "nb64")] = dict(r)
+            if name not in res or r["median_s"] < res[name]["median_s"]:
+                res[name] = r
     q.qr_set_option(q.QR_OPT_LS_REFINE, 0)
     # the FP32-storage factorization alone, FP32 cores vs tensor cores
     fac = {}
