@@ -292,13 +292,18 @@ def run_ls(args):
             nb, ib = args.nb, args.ib
         pd = args.ls_p if args.ls_p else pd
         tol = args.ls_tol if prec != q.QR_PREC_F64 else 2.0 ** -52
-        # the FP64 baseline: the factorization table's pair, and, when its
-        # tiles are larger than 64, NB = 64 with the same IB and the library's
-        # domain count (the few-column Q applications stage 64-row tiles
-        # whole); the faster solve is the baseline, both are reported
+        # every solve at the faster of a few configurations, all reported:
+        # the factorization table's (NB, IB, p); the same pair with the
+        # library's domain count (p = 0: ceil(MT / NT), shorter Q-application
+        # chains); and, when the table's tiles are larger than 64, NB = 64
+        # with the same IB (the few-column Q applications stage 64-row tiles
+        # whole)
         cands = [(nb, ib, pd)]
-        if prec == q.QR_PREC_F64 and not args.nb and nb > 64:
-            cands.append((64, ib, 0))
+        if not args.nb and not args.ls_p:
+            cands.append((nb, ib, 0))
+            if nb > 64:
+                cands.append((64, ib, 0))
+        labels = ["table", "p_default", "nb64"]
         for ci, (nb_c, ib_c, p_c) in enumerate(cands):
             X, info = q.qr_solve_ls(A, B, prec=prec, nb=nb_c, ib=ib_c, max_iter=it, tol=tol, p=p_c)  # warm-up
             torch.cuda.synchronize()
@@ -312,7 +317,7 @@ def run_ls(args):
                  "refine": ["none", "augmented", "gmres"][refine] if prec != q.QR_PREC_F64 else "none",
                  "X": X.cpu().numpy()}
             if len(cands) > 1:
-                res["%s_%s" % (name, "table_pair" if ci == 0 else "nb64")] = dict(r)
+                res["%s_%s" % (name, labels[ci])] = dict(r)
             if name not in res or r["median_s"] < res[name]["median_s"]:
                 res[name] = r
     q.qr_set_option(q.QR_OPT_LS_REFINE, 0)

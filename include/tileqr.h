@@ -366,7 +366,10 @@ int qr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double *d_A, int64_t l
  *   8 <= IB <= NB/2 (119 pairs), up to 50 launches each (Sec. 5);
  *   Property 5.1 (best IB per NB), Property 5.2 (upper convex hull) and
  *   Heuristic `heuristic` (0, 1 or 2; 2 is the paper's default) preselect at
- *   most 8 pairs; Step 2 = time qr_factor for the survivors at every shape,
+ *   most 8 pairs (with QR_OPT_TUNE_IB_TOL > 0 each preselected NB also
+ *   brings the IBs within that tolerance of its best IB's rate, a widening
+ *   of Property 5.1 that this library adds); Step 2 = time qr_factor for the
+ *   survivors at every shape,
  *   ascending n, `reps` runs each (median; the paper uses 6, Sec. 6.1), and
  *   prune as you go with Property 6.1 between square orders (Sec. 6.3).
  *   For tall-skinny shapes (m >= 4n, at least 4 tile rows) the chosen pair
