@@ -18,6 +18,9 @@ Contents:
   * ``tile_apply.py`` -- Q^T of a flat-tree tile QR applied in NumPy from
     stored factors (reflectors and T blocks): the large-N probe that checks
     the GPU's stored factors independently of its Q-application kernels.
+  * ``lu.py`` -- tile LU with incremental (pairwise) pivoting written out task
+    by task (GETRF, GESSM, TSTRF, SSSSM) with NumPy row operations, the
+    transformations applied to other columns, back substitution.
 
 The paper is Agullo, Dongarra, Nath, Tomov, "A Fully Empirical Autotuned
 Dense QR Factorization for Multicore Architectures" (INRIA RR-7526).
