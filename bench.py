@@ -425,6 +425,61 @@ def run_cholesky(args):
     return 0
 
 
+def run_lu(args):
+    """FP64 tile LU with incremental pivoting (lu_factor_d) of a uniform
+    [-0.5, 0.5) matrix of order --n, nb = --nb or 64: GFLOP/s credited
+    2 n^3 / 3, CUDA events around each call (layout conversions included),
+    against the FP64 FMA peak; the CPU oracle's task-by-task tile LU on a
+    bounded sample (order 1000)."""
+    import torch
+
+    import paper_1102_5328_gb300 as q
+    from paper_1102_5328_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    n = args.n
+    A_np = inputs.uniform_matrix(n, n, seed=n)
+    A0 = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()
+    A = A0.clone()
+    nb = args.nb or 64
+    f = q.lu_factor(A, nb)
+    ms = []
+    for s in range(args.warmup + args.steps):
+        A.copy_(A0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        q.lu_factor(A, nb, piv=f.piv, scratch=f.scratch)
+        e1.record()
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    st = f.status()
+    flops = 2.0 * float(n) ** 3 / 3.0
+    med = statistics.median(ms)
+    peak_live = q.qr_peak_fp64()
+    nominal_peak = 152 * 2 * 2 * 2.070e9 / 1e9
+    line = {"workload": "fp64 tile LU (incremental pivoting), N=%d, uniform[-0.5,0.5)" % n,
+            "metric": "LU GFlop/s (2n^3/3)/t", "value": flops / (med * 1e-3) / 1e9, "unit": "GFLOP/s",
+            "ms_per_step": med, "steps": args.steps, "nb": nb, "status": list(st),
+            "tasks": int(q.lib().lu_task_count_n(n, nb)),
+            "roofline": {"bound": "alu", "peak": nominal_peak, "unit": "GFLOP/s",
+                         "frac": flops / (med * 1e-3) / 1e9 / nominal_peak,
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                         "peak_measured_live": peak_live}}
+    if not args.no_cpu:
+        from oracle import lu
+        ns = 1000
+        S = inputs.uniform_matrix(ns, ns, seed=ns)
+        t0 = time.perf_counter()
+        lu.getrf_incpiv(S, nb)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 2.0 * ns ** 3 / 3.0 / dt / 1e9, "unit": "GFLOP/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "tile LU of order %d, NB %d, NumPy row operations (%.1f s)" % (ns, nb, dt)}
+    print(json.dumps(line))
+    return 0
+
+
 def run_step1(args):
     """The Step-1 kernel benchmark (Sec. 5) for one (NB, IB): a batch of
     2 x SMs independent TSMQR tasks per launch, No Flush; GFLOP/s credits
@@ -473,7 +528,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--prec", default="f64", choices=["f64", "f32", "tf32", "bf16x3"],
                     help="step1: precision of the TSMQR batch (tf32 / bf16x3: FP32 tiles, tensor-core products)")
-    ap.add_argument("--workload", default="qr", choices=["qr", "batched", "ls", "step1", "cholesky"],
+    ap.add_argument("--workload", default="qr", choices=["qr", "batched", "ls", "step1", "cholesky", "lu"],
                     help="qr: the headline line; batched / ls: the extension workloads (own JSON lines)")
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--ls-m", type=int, default=16384)
@@ -492,6 +547,8 @@ def main():
         return run_ls(args)
     if args.workload == "step1":
         return run_step1(args)
+    if args.workload == "lu":
+        return run_lu(args)
     if args.workload == "cholesky":
         return run_cholesky(args)
 

@@ -47,6 +47,7 @@ extern "C" {
 #define QR_DEV_TIMEOUT   1 /* a scheduler dependency wait ran out of time */
 #define QR_DEV_NONFINITE 2 /* a column norm or pivot was Inf/NaN */
 #define QR_DEV_NOT_SPD   4 /* Cholesky: a pivot was not positive (chol_status gives the first such column) */
+#define QR_DEV_SINGULAR  8 /* LU: a pivot was zero (lu_status gives the first such column) */
 
 /* Options (qr_set_option). */
 #define QR_OPT_WAIT_TIMEOUT_US 1 /* per-wait limit of the persistent scheduler (default 20 s) */
@@ -561,6 +562,41 @@ int chol_workspace(int64_t n, int nb, int64_t *bytes);
 int chol_factor_d(int64_t n, double *d_A, int64_t lda, int nb, void *d_scratch, int64_t scratch_bytes, void *stream);
 int chol_status(const void *d_scratch, int *status, int64_t *first_bad_col, void *stream);
 int64_t chol_task_count_n(int64_t n, int nb);
+
+/*
+ * lu_workspace / lu_factor_d -- FP64 tile LU with incremental (pairwise)
+ * pivoting of the n x n matrix A (column-major, lda >= n), in place: the LU
+ * the paper names beside Cholesky as carrying its tile framework and tuning
+ * method (Secs. 1 and 7; it defines no LU algorithm). Tasks, the flat-tree
+ * DAG of the tile QR with LU kernels: GETRF(k) (partial pivoting inside the
+ * diagonal tile), GESSM(k, j) (its swaps and eliminations applied to A_kj),
+ * TSTRF(i, k) (pairwise-pivoted LU of [U_kk; A_ik]: a row of A_ik replaces
+ * U_kk's row c when its |entry| in column c is strictly larger, first such
+ * row on ties), SSSSM(i, j, k) (those swaps and eliminations applied to
+ * [A_kj; A_ij]); swaps move columns c.. only. On return A holds U on and
+ * above the diagonal and each task's multipliers below it (a sequence of
+ * elementary transformations, not L of one row permutation).
+ * d_piv (int32, lu_workspace's piv_elems, caller-owned output): tile (i, k)
+ * column c at d_piv[(k * NT + i) * nb + c], NT = ceil(n / nb): GETRF the
+ * tile row swapped with row c (c when none), TSTRF the row of A_ik swapped
+ * with U_kk's row c (-1 when none); entries past a short last tile are not
+ * written. nb in [8, 64] (0 = 64). d_scratch (lu_workspace's scratch_bytes:
+ * control block, counters, task list, tile copy of A) caller-owned. One
+ * persistent kernel in a list-scheduled ticket order with bounded waits on
+ * per-tile operation counters; layout conversions before and after. A zero
+ * pivot sets QR_DEV_SINGULAR and its column is skipped (no division), as
+ * LAPACK's getrf continues past one. Errors: -1 n, -2 A, -3 lda, -4 nb,
+ * -5 no d_piv, -6 no scratch, -7 scratch too small.
+ * lu_status: synchronises `stream`; *status gets the QR_DEV_* bits of the
+ * last factorization that used d_scratch, *first_zero_col (may be NULL) the
+ * smallest column whose pivot was zero, or -1.
+ * lu_task_count_n: tasks of the DAG for (n, nb), -1 for bad arguments.
+ */
+int lu_workspace(int64_t n, int nb, int64_t *piv_elems, int64_t *scratch_bytes);
+int lu_factor_d(int64_t n, double *d_A, int64_t lda, int nb, int *d_piv, void *d_scratch, int64_t scratch_bytes,
+                void *stream);
+int lu_status(const void *d_scratch, int *status, int64_t *first_zero_col, void *stream);
+int64_t lu_task_count_n(int64_t n, int nb);
 
 /*
  * The Cholesky tuner (Secs. 5–6 applied to the one tuning parameter NB).

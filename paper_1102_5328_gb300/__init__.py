@@ -25,6 +25,7 @@ QR_PREC_BF16X3 = 3
 QR_DEV_TIMEOUT = 1
 QR_DEV_NONFINITE = 2
 QR_DEV_NOT_SPD = 4
+QR_DEV_SINGULAR = 8
 QR_OPT_WAIT_TIMEOUT_US = 1
 QR_OPT_CTAS_PER_SM = 2
 QR_OPT_SPLIT = 3
@@ -462,6 +463,46 @@ def chol_factor(A, nb=0, scratch=None, stream=None):
     _lib.check(lib().chol_factor_d(n, ctypes.c_void_p(A.data_ptr()), lda, nb, ctypes.c_void_p(scratch.data_ptr()),
                                    b.value, _stream_ptr(stream)), "chol_factor_d")
     return CholFactorization(A, scratch, nb)
+
+
+class LUFactorization:
+    """Result of lu_factor: A with U on and above its diagonal and the
+    multipliers below, the pivot records (int32, tile (i, k) at
+    piv[(k * NT + i) * nb + c]) and the scratch buffer (device status)."""
+
+    def __init__(self, A, piv, scratch, nb):
+        self.A, self.piv, self.scratch, self.nb = A, piv, scratch, nb
+
+    def status(self, stream=None):
+        """(QR_DEV_* bits, first column whose pivot was zero or -1)."""
+        st, col = ctypes.c_int(), ctypes.c_int64()
+        _lib.check(lib().lu_status(ctypes.c_void_p(self.scratch.data_ptr()), ctypes.byref(st), ctypes.byref(col),
+                                   _stream_ptr(stream)), "lu_status")
+        return st.value, col.value
+
+
+def lu_workspace(n, nb=0):
+    """(pivot-record elements, scratch bytes) for lu_factor."""
+    pe, sb = ctypes.c_int64(), ctypes.c_int64()
+    _lib.check(lib().lu_workspace(n, nb, ctypes.byref(pe), ctypes.byref(sb)), "lu_workspace")
+    return pe.value, sb.value
+
+
+def lu_factor(A, nb=0, piv=None, scratch=None, stream=None):
+    """Tile LU with incremental pivoting of the square float64 column-major
+    CUDA tensor A, in place. nb in [8, 64]; 0 takes 64."""
+    n = A.shape[0]
+    if A.dtype != torch.float64 or not A.is_cuda or A.stride(0) != 1 or A.shape[1] != n:
+        raise ValueError("A must be a square column-major float64 CUDA tensor")
+    pe, sb = lu_workspace(n, nb)
+    if piv is None or piv.numel() < pe:
+        piv = torch.full((max(pe, 1),), -1, dtype=torch.int32, device=A.device)
+    if scratch is None or scratch.numel() < sb:
+        scratch = torch.empty(sb, dtype=torch.uint8, device=A.device)
+    lda = A.stride(1) if n > 1 else max(n, 1)
+    _lib.check(lib().lu_factor_d(n, ctypes.c_void_p(A.data_ptr()), lda, nb, ctypes.c_void_p(piv.data_ptr()),
+                                 ctypes.c_void_p(scratch.data_ptr()), sb, _stream_ptr(stream)), "lu_factor_d")
+    return LUFactorization(A, piv, scratch, nb if nb else 64)
 
 
 def chol_tune(ns, heuristic=2, reps=6, table="", log="", stream=None):

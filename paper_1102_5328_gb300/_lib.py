@@ -92,6 +92,10 @@ SIGNATURES = [
                           ctypes.POINTER(c_dbl), c_vp]),
     ("chol_load_table", c_int, [ctypes.c_char_p]),
     ("chol_lookup", c_int, [c_i64, ctypes.POINTER(c_int)]),
+    ("lu_workspace", c_int, [c_i64, c_int, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    ("lu_factor_d", c_int, [c_i64, c_vp, c_i64, c_int, c_vp, c_vp, c_i64, c_vp]),
+    ("lu_status", c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), c_vp]),
+    ("lu_task_count_n", c_i64, [c_i64, c_int]),
     ("qr_model_propose", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
     ("qr_peak_fp64", c_int, [ctypes.POINTER(c_dbl), c_vp]),
