@@ -427,7 +427,7 @@ def run_cholesky(args):
 
 def run_lu(args):
     """FP64 tile LU with incremental pivoting (lu_factor_d) of a uniform
-    [-0.5, 0.5) matrix of order --n, nb = --nb or 64: GFLOP/s credited
+    [-0.5, 0.5) matrix of order --n, nb from the LU tuning table (or --nb): GFLOP/s credited
     2 n^3 / 3, CUDA events around each call (layout conversions included),
     against the FP64 FMA peak; the CPU oracle's task-by-task tile LU on a
     bounded sample (order 1000)."""
@@ -441,7 +441,12 @@ def run_lu(args):
     A_np = inputs.uniform_matrix(n, n, seed=n)
     A0 = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()
     A = A0.clone()
-    nb = args.nb or 64
+    nb = args.nb
+    if not nb:
+        import ctypes
+        v = ctypes.c_int()
+        q.lib().lu_lookup(n, ctypes.byref(v))
+        nb = v.value
     f = q.lu_factor(A, nb)
     ms = []
     for s in range(args.warmup + args.steps):

@@ -580,7 +580,7 @@ int64_t chol_task_count_n(int64_t n, int nb);
  * column c at d_piv[(k * NT + i) * nb + c], NT = ceil(n / nb): GETRF the
  * tile row swapped with row c (c when none), TSTRF the row of A_ik swapped
  * with U_kk's row c (-1 when none); entries past a short last tile are not
- * written. nb in [8, 64] (0 = 64). d_scratch (lu_workspace's scratch_bytes:
+ * written. nb in [8, 64] (0 = the LU tuning table; 64 without one). d_scratch (lu_workspace's scratch_bytes:
  * control block, counters, task list, tile copy of A) caller-owned. One
  * persistent kernel in a list-scheduled ticket order with bounded waits on
  * per-tile operation counters; layout conversions before and after. A zero
@@ -597,6 +597,40 @@ int lu_factor_d(int64_t n, double *d_A, int64_t lda, int nb, int *d_piv, void *d
                 void *stream);
 int lu_status(const void *d_scratch, int *status, int64_t *first_zero_col, void *stream);
 int64_t lu_task_count_n(int64_t n, int nb);
+
+/*
+ * The LU's NB tuner (Secs. 5–6 applied to its one tuning parameter, as for
+ * the Cholesky).
+ * lu_step1_time: Step 1 -- `launches` back-to-back launches (<= 0: enough
+ *   for ~30 ms, 3 to 50) of a batch of 2 x (SM count) independent SSSSM tile
+ *   tasks of order nb (the dominant task; every other column swaps), same
+ *   data every launch; *seconds_per_launch, *gflops (2 nb^3 per task, may be
+ *   NULL). d_work: lu_step1_workspace bytes. Errors: -1 nb (8..64), -3
+ *   output, -5 no d_work, -7 d_work too small.
+ * lu_time_factor: Step 2 -- reps timed lu_factor_d calls on fresh uniform
+ *   [-0.5, 0.5) matrices of order n generated on the device (median and
+ *   minimum seconds; the refill is not timed). d_work: lu_tune_workspace
+ *   bytes for an order >= n.
+ * lu_tune: Step 1 over NB in {16, 24, ..., 64}, the upper hull and Heuristic
+ *   `heuristic` (qr_tune_preselect with IB fixed), Step 2 over the orders
+ *   ns[] ascending with prune-as-you-go (qr_tune_payg), `reps` runs each;
+ *   logs kind 21 (Step 1) and 22 (Step 2) to log_path (resumes from it),
+ *   writes the table to table_path and installs it in-process.
+ *   seconds_out[4]: total, Step 1, Step 2, factorizations timed.
+ * lu_load_table / lu_lookup / lu_clear_table: the table lu_factor_d uses
+ *   for nb = 0 (closest tuned order, ties to the smaller; 64 without one).
+ */
+int lu_step1_workspace(int nb, int64_t *bytes);
+int lu_step1_time(int nb, int launches, double *seconds_per_launch, double *gflops, void *d_work, int64_t work_bytes,
+                  void *stream);
+int lu_time_factor(int64_t n, int nb, int reps, double *median_s, double *min_s, void *d_work, int64_t work_bytes,
+                   void *stream);
+int lu_tune_workspace(int64_t max_n, int64_t *bytes);
+int lu_tune(const int64_t *ns, int nshapes, int heuristic, int reps, const char *table_path, const char *log_path,
+            void *d_work, int64_t work_bytes, double *seconds_out, void *stream);
+int lu_load_table(const char *path);
+int lu_lookup(int64_t n, int *nb);
+int lu_clear_table(void);
 
 /*
  * The Cholesky tuner (Secs. 5–6 applied to the one tuning parameter NB).

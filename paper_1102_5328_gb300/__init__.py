@@ -69,6 +69,9 @@ def lib():
         path = os.path.join(_TUNED_DIR, "gb300_chol_fp64.json")
         if os.path.exists(path):
             L.chol_load_table(path.encode())
+        path = os.path.join(_TUNED_DIR, "gb300_lu_fp64.json")
+        if os.path.exists(path):
+            L.lu_load_table(path.encode())
         path = os.path.join(_TUNED_DIR, "gb300_batched_classes.json")
         if os.path.exists(path):
             with open(path) as f:
@@ -490,10 +493,15 @@ def lu_workspace(n, nb=0):
 
 def lu_factor(A, nb=0, piv=None, scratch=None, stream=None):
     """Tile LU with incremental pivoting of the square float64 column-major
-    CUDA tensor A, in place. nb in [8, 64]; 0 takes 64."""
+    CUDA tensor A, in place. nb in [8, 64]; 0 takes the LU tuning table's
+    (64 without one)."""
     n = A.shape[0]
     if A.dtype != torch.float64 or not A.is_cuda or A.stride(0) != 1 or A.shape[1] != n:
         raise ValueError("A must be a square column-major float64 CUDA tensor")
+    if nb == 0:
+        nbv = ctypes.c_int()
+        _lib.check(lib().lu_lookup(n, ctypes.byref(nbv)), "lu_lookup")
+        nb = nbv.value
     pe, sb = lu_workspace(n, nb)
     if piv is None or piv.numel() < pe:
         piv = torch.full((max(pe, 1),), -1, dtype=torch.int32, device=A.device)
@@ -502,7 +510,21 @@ def lu_factor(A, nb=0, piv=None, scratch=None, stream=None):
     lda = A.stride(1) if n > 1 else max(n, 1)
     _lib.check(lib().lu_factor_d(n, ctypes.c_void_p(A.data_ptr()), lda, nb, ctypes.c_void_p(piv.data_ptr()),
                                  ctypes.c_void_p(scratch.data_ptr()), sb, _stream_ptr(stream)), "lu_factor_d")
-    return LUFactorization(A, piv, scratch, nb if nb else 64)
+    return LUFactorization(A, piv, scratch, nb)
+
+
+def lu_tune(ns, heuristic=2, reps=6, table="", log="", stream=None):
+    """The LU NB tuner (lu_tune); returns its wall-time figures."""
+    L = lib()
+    b = ctypes.c_int64()
+    _lib.check(L.lu_tune_workspace(max(ns), ctypes.byref(b)), "lu_tune_workspace")
+    work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+    arr = (ctypes.c_int64 * len(ns))(*ns)
+    secs = (ctypes.c_double * 4)()
+    _lib.check(L.lu_tune(arr, len(ns), heuristic, reps, table.encode(), log.encode(), ctypes.c_void_p(work.data_ptr()),
+                         b.value, secs, _stream_ptr(stream)), "lu_tune")
+    return {"seconds": secs[0], "step1_seconds": secs[1], "step2_seconds": secs[2], "factorizations_timed": int(secs[3]),
+            "heuristic": heuristic, "reps": reps, "ns": list(ns), "table": table, "log": log}
 
 
 def chol_tune(ns, heuristic=2, reps=6, table="", log="", stream=None):

@@ -96,6 +96,15 @@ SIGNATURES = [
     ("lu_factor_d", c_int, [c_i64, c_vp, c_i64, c_int, c_vp, c_vp, c_i64, c_vp]),
     ("lu_status", c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), c_vp]),
     ("lu_task_count_n", c_i64, [c_i64, c_int]),
+    ("lu_step1_workspace", c_int, [c_int, ctypes.POINTER(c_i64)]),
+    ("lu_step1_time", c_int, [c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
+    ("lu_time_factor", c_int, [c_i64, c_int, c_int, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
+    ("lu_tune_workspace", c_int, [c_i64, ctypes.POINTER(c_i64)]),
+    ("lu_tune", c_int, [ctypes.POINTER(c_i64), c_int, c_int, c_int, ctypes.c_char_p, ctypes.c_char_p, c_vp, c_i64,
+                        ctypes.POINTER(c_dbl), c_vp]),
+    ("lu_load_table", c_int, [ctypes.c_char_p]),
+    ("lu_lookup", c_int, [c_i64, ctypes.POINTER(c_int)]),
+    ("lu_clear_table", c_int, []),
     ("qr_model_propose", c_int, [c_i64, c_i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_dbl), c_vp, c_i64, c_vp]),
     ("qr_peak_fp64", c_int, [ctypes.POINTER(c_dbl), c_vp]),

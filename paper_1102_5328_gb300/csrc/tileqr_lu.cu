@@ -24,11 +24,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -38,6 +43,10 @@
 #include "tileqr_internal.h"
 
 using namespace tqr;
+
+// nb for an order n from the LU tuning table (closest tuned order, ties to
+// the smaller); 64 when nothing is tuned (returns 1 then).
+int lu_table_lookup(int64_t n, int* nb);
 
 namespace {
 
@@ -510,7 +519,7 @@ int lu_impl(int64_t n, double* A, int64_t lda, int nb, int* d_piv, void* scratch
   if (n < 0) return -1;
   if (!A && n > 0) return -2;
   if (lda < std::max<int64_t>(n, 1)) return -3;
-  if (nb == 0) nb = LMAX;
+  if (nb == 0) lu_table_lookup(n, &nb);
   if (int rc = lu_args_check(n, nb)) return rc;
   if (n == 0) return 0;
   if (!d_piv) return -5;
@@ -549,12 +558,190 @@ int lu_impl(int64_t n, double* A, int64_t lda, int nb, int* d_piv, void* scratch
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// The empirical NB tuner of the LU, Secs. 5–6 applied to its one tuning
+// parameter: Step 1 times the dominant task (SSSSM, about NT^3 / 3 of them)
+// on a device-filling batch for every NB of the grid {16, 24, ..., 64}; the
+// upper hull of (NB, GFLOP/s) and Heuristic 0/1/2 (qr_tune_preselect)
+// preselect; Step 2 times the factorization for the survivors at each
+// order, ascending, and prunes with Property 6.1 (qr_tune_payg); untuned
+// orders take the closest tuned one.
+__global__ void __launch_bounds__(LT, 2) ssssm_batch(double* X, double* Y, const double* L, const int* piv, int NB) {
+  extern __shared__ __align__(16) double bsm_raw[];
+  __shared__ int s_piv[LMAX];
+  __shared__ int s_pick;
+  LSm sm;
+  sm.s1 = bsm_raw;
+  sm.s2 = bsm_raw + LMAX * LLD;
+  sm.piv = s_piv;
+  sm.pick = &s_pick;
+  const size_t te = (size_t)NB * NB;
+  ssssm_task(X + blockIdx.x * te, Y + blockIdx.x * te, L, NB, NB, piv, sm);
+}
+
+__device__ __forceinline__ double lu_hash_unit(uint64_t x) {
+  // SplitMix64 finalizer (Steele, Lea, Flood 2014) -> uniform in [0, 1)
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void lu_fill(double* p, int64_t cnt, uint64_t seed) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = lu_hash_unit(seed * 0x100000001B3ull + (uint64_t)e) - 0.5;
+}
+
+// Step-1 pivot records: every other column swaps with a row of the tile
+// below, the others keep U's row (random matrices swap about that often).
+__global__ void lu_fill_piv(int* piv, int NB) {
+  for (int c = threadIdx.x; c < NB; c += blockDim.x) piv[c] = (c & 1) ? -1 : (c * 7) % NB;
+}
+
+int lu_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  return sms;
+}
+
+int64_t lu_step1_bytes(int nb) { return (int64_t)(1 + 4 * (int64_t)lu_sms()) * nb * nb * 8 + 256 + 4 * LMAX; }
+
+int lu_step1_run(int nb, int launches, double* sec, void* work, int64_t wbytes, cudaStream_t st) {
+  const int nbatch = 2 * lu_sms();
+  if (lu_step1_bytes(nb) > wbytes) return -7;
+  const size_t te = (size_t)nb * nb;
+  int* piv = (int*)work;
+  double* L = (double*)((char*)work + 256 + 4 * LMAX);
+  double* X = L + te;
+  double* Y = X + nbatch * te;
+  lu_fill<<<1024, 256, 0, st>>>(L, (int64_t)(1 + 2 * nbatch) * te, 23);
+  lu_fill_piv<<<1, 64, 0, st>>>(piv, nb);
+  cudaError_t e = cudaFuncSetAttribute(ssssm_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLSmemBytes);
+  if (e != cudaSuccess) return (int)e;
+  ssssm_batch<<<nbatch, LT, kLSmemBytes, st>>>(X, Y, L, piv, nb);  // warm-up
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  if (launches <= 0) {  // as many launches as fill ~30 ms, 3 to the paper's 50
+    cudaEventRecord(e0, st);
+    ssssm_batch<<<nbatch, LT, kLSmemBytes, st>>>(X, Y, L, piv, nb);
+    cudaEventRecord(e1, st);
+    float ms1 = 1.f;
+    if ((e = cudaEventSynchronize(e1)) == cudaSuccess) e = cudaEventElapsedTime(&ms1, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return (int)e;
+    }
+    launches = std::max(3, std::min(50, (int)std::ceil(30.0 / std::max(ms1, 1e-3f))));
+  }
+  cudaEventRecord(e0, st);
+  for (int l = 0; l < launches; ++l) ssssm_batch<<<nbatch, LT, kLSmemBytes, st>>>(X, Y, L, piv, nb);
+  cudaEventRecord(e1, st);
+  float ms = 0.f;
+  if ((e = cudaEventSynchronize(e1)) == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return (int)e;
+  *sec = ms * 1e-3 / launches;
+  return 0;
+}
+
+// reps timed factorizations of a fresh uniform matrix of order n (CUDA
+// events around each call; the refill is outside them); median and minimum
+// seconds. work holds A, the pivot records, then the scratch.
+int time_lu(int64_t n, int nb, int reps, void* work, int64_t wbytes, cudaStream_t st, double* med, double* mn) {
+  const size_t a_bytes = al256l((size_t)n * n * 8);
+  const LLayout L = lu_layout(n, nb);
+  const size_t p_bytes = al256l((size_t)L.NT * L.NT * nb * 4);
+  if ((int64_t)(a_bytes + p_bytes + L.bytes) > wbytes) return -7;
+  double* A = (double*)work;
+  int* piv = (int*)((char*)work + a_bytes);
+  void* scr = (char*)work + a_bytes + p_bytes;
+  std::vector<double> ts;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int warm = n * n <= 4000000 ? 1 : 0;
+  int rc = 0;
+  for (int r = 1 - warm; r < reps + 1; ++r) {
+    lu_fill<<<1184, 256, 0, st>>>(A, n * n, (uint64_t)n * 131 + 11);
+    cudaEventRecord(e0, st);
+    rc = lu_impl(n, A, n, nb, piv, scr, (int64_t)L.bytes, st);
+    cudaEventRecord(e1, st);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      rc = (int)e;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    int stat = 0;
+    if ((e = cudaMemcpy(&stat, scr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      rc = (int)e;
+      break;
+    }
+    if (stat) {
+      rc = 1000 + stat;
+      break;
+    }
+    if (r > 0) ts.push_back(ms * 1e-3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  std::sort(ts.begin(), ts.end());
+  *med = ts.size() % 2 ? ts[ts.size() / 2] : 0.5 * (ts[ts.size() / 2 - 1] + ts[ts.size() / 2]);
+  *mn = ts.front();
+  return 0;
+}
+
+struct LEntry {
+  int64_t n;
+  int nb;
+  double gflops;
+};
+std::mutex g_ltmu;
+std::vector<LEntry> g_ltab;
+
+void lu_append_log(const char* path, int kind, int64_t n, int nb, double sec, double smin, int reps) {
+  if (!path || !path[0]) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"kind\": %d, \"n\": %lld, \"nb\": %d, \"seconds\": %.9g, \"min\": %.9g, \"reps\": %d}\n", kind,
+          (long long)n, nb, sec, smin, reps);
+  fclose(f);
+}
+
+void lu_read_log(const char* path, std::map<std::tuple<int, int64_t, int>, double>* seen) {
+  if (!path || !path[0]) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    int kind, nb;
+    long long n;
+    double sec;
+    if (sscanf(line, "{\"kind\": %d, \"n\": %lld, \"nb\": %d, \"seconds\": %lf", &kind, &n, &nb, &sec) == 4)
+      (*seen)[std::make_tuple(kind, (int64_t)n, nb)] = sec;
+  }
+  fclose(f);
+}
+
+bool lu_nb_ok(int nb) { return nb >= 8 && nb <= LMAX; }
+
 }  // namespace
 
 extern "C" {
 
 int lu_workspace(int64_t n, int nb, int64_t* piv_elems, int64_t* scratch_bytes) {
-  if (nb == 0) nb = LMAX;
+  if (nb == 0) lu_table_lookup(n, &nb);
   if (int rc = lu_args_check(n, nb)) return rc;
   const LLayout L = lu_layout(std::max<int64_t>(n, 1), nb);
   if (piv_elems) *piv_elems = (int64_t)L.NT * L.NT * nb;
@@ -563,7 +750,7 @@ int lu_workspace(int64_t n, int nb, int64_t* piv_elems, int64_t* scratch_bytes) 
 }
 
 int64_t lu_task_count_n(int64_t n, int nb) {
-  if (nb == 0) nb = LMAX;
+  if (nb == 0) lu_table_lookup(n, &nb);
   if (lu_args_check(n, nb)) return -1;
   return lu_task_count((int)((n + nb - 1) / nb));
 }
@@ -588,4 +775,196 @@ int lu_status(const void* d_scratch, int* status, int64_t* first_zero_col, void*
   return 0;
 }
 
+int lu_step1_workspace(int nb, int64_t* bytes) {
+  if (!lu_nb_ok(nb)) return -1;
+  if (!bytes) return -2;
+  *bytes = lu_step1_bytes(nb);
+  return 0;
+}
+
+int lu_step1_time(int nb, int launches, double* seconds_per_launch, double* gflops, void* d_work, int64_t work_bytes,
+                  void* stream) {
+  if (!lu_nb_ok(nb)) return -1;
+  if (!seconds_per_launch) return -3;
+  if (!d_work) return -5;
+  double s = 0;
+  const int rc = lu_step1_run(nb, launches, &s, d_work, work_bytes, (cudaStream_t)stream);
+  if (rc) return rc;
+  *seconds_per_launch = s;
+  if (gflops) *gflops = 2.0 * lu_sms() * 2.0 * nb * (double)nb * nb / s / 1e9;
+  return 0;
+}
+
+int lu_time_factor(int64_t n, int nb, int reps, double* median_s, double* min_s, void* d_work, int64_t work_bytes,
+                   void* stream) {
+  if (n < 1) return -1;
+  if (!lu_nb_ok(nb)) return -2;
+  if (reps < 1) return -3;
+  if (!median_s || !min_s) return -4;
+  if (!d_work) return -6;
+  return time_lu(n, nb, reps, d_work, work_bytes, (cudaStream_t)stream, median_s, min_s);
+}
+
+int lu_tune_workspace(int64_t max_n, int64_t* bytes) {
+  if (max_n < 1 || (max_n + 7) / 8 > 65535) return -1;
+  if (!bytes) return -2;
+  int64_t best = lu_step1_bytes(LMAX);
+  for (int nb = 16; nb <= LMAX; nb += 8) {
+    const LLayout L = lu_layout(max_n, nb);
+    best = std::max<int64_t>(best, (int64_t)(al256l((size_t)max_n * max_n * 8) +
+                                              al256l((size_t)L.NT * L.NT * nb * 4) + L.bytes));
+  }
+  *bytes = best;
+  return 0;
+}
+
+int lu_tune(const int64_t* ns, int nshapes, int heuristic, int reps, const char* table_path, const char* log_path,
+            void* d_work, int64_t work_bytes, double* seconds_out, void* stream) {
+  if (!ns || nshapes < 1) return -1;
+  if (heuristic < 0 || heuristic > 2) return -3;
+  if (reps < 1) return -4;
+  if (!d_work) return -7;
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto t_start = std::chrono::steady_clock::now();
+  auto since = [](std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  };
+  std::map<std::tuple<int, int64_t, int>, double> seen;
+  lu_read_log(log_path, &seen);
+  std::vector<int> grid;
+  for (int nb = 16; nb <= LMAX; nb += 8) grid.push_back(nb);
+  std::vector<int> ibs(grid.size(), 1);
+  std::vector<double> perf(grid.size());
+  double step1_s = 0, step2_s = 0;
+  int measured = 0;
+  for (size_t g = 0; g < grid.size(); ++g) {
+    double s = 0, gf = 0;
+    auto it = seen.find(std::make_tuple(21, (int64_t)0, grid[g]));
+    if (it != seen.end()) {
+      s = it->second;
+    } else {
+      const auto t0 = std::chrono::steady_clock::now();
+      int rc = lu_step1_time(grid[g], 0, &s, &gf, d_work, work_bytes, stream);
+      if (rc) return rc;
+      step1_s += since(t0);
+      lu_append_log(log_path, 21, 0, grid[g], s, s, 0);
+    }
+    perf[g] = 2.0 * lu_sms() * 2.0 * grid[g] * (double)grid[g] * grid[g] / s / 1e9;
+  }
+  std::vector<int> snb(grid.size()), sib(grid.size());
+  const int k = qr_tune_preselect((int)grid.size(), grid.data(), ibs.data(), perf.data(), heuristic, 8, 8, snb.data(),
+                                  sib.data());
+  if (k < 1) return -8;
+  std::vector<int> surv(snb.begin(), snb.begin() + k);
+  std::vector<int64_t> order(ns, ns + nshapes);
+  std::sort(order.begin(), order.end());
+  std::vector<LEntry> table;
+  for (int64_t n : order) {
+    std::vector<double> pf(surv.size());
+    for (size_t c = 0; c < surv.size(); ++c) {
+      double med = 0, mn = 0;
+      auto it = seen.find(std::make_tuple(22, n, surv[c]));
+      if (it != seen.end()) {
+        med = it->second;
+      } else {
+        const auto t0 = std::chrono::steady_clock::now();
+        int rc = time_lu(n, surv[c], reps, d_work, work_bytes, st, &med, &mn);
+        if (rc) return rc;
+        step2_s += since(t0);
+        lu_append_log(log_path, 22, n, surv[c], med, mn, reps);
+        ++measured;
+      }
+      pf[c] = 2.0 * (double)n * n * n / 3.0 / med / 1e9;
+    }
+    size_t bi = 0;
+    for (size_t c = 1; c < surv.size(); ++c)
+      if (pf[c] > pf[bi] || (pf[c] == pf[bi] && surv[c] < surv[bi])) bi = c;
+    table.push_back(LEntry{n, surv[bi], pf[bi]});
+    std::vector<int> keep(surv.size());
+    qr_tune_payg((int)surv.size(), surv.data(), pf.data(), keep.data());  // Property 6.1
+    std::vector<int> nx;
+    for (size_t c = 0; c < surv.size(); ++c)
+      if (keep[c]) nx.push_back(surv[c]);
+    surv = nx;
+  }
+  const double total = since(t_start);
+  if (seconds_out) {
+    seconds_out[0] = total;
+    seconds_out[1] = step1_s;
+    seconds_out[2] = step2_s;
+    seconds_out[3] = measured;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_ltmu);
+    g_ltab = table;
+  }
+  if (table_path && table_path[0]) {
+    FILE* f = fopen(table_path, "w");
+    if (!f) return -5;
+    fprintf(f, "{\n  \"factorization\": \"lu\",\n  \"heuristic\": %d,\n  \"reps\": %d,\n  \"seconds\": %.3f,\n"
+               "  \"step1_seconds\": %.3f,\n  \"step2_seconds\": %.3f,\n  \"entries\": [\n",
+            heuristic, reps, total, step1_s, step2_s);
+    for (size_t i = 0; i < table.size(); ++i)
+      fprintf(f, "    {\"n\": %lld, \"nb\": %d, \"gflops\": %.4f}%s\n", (long long)table[i].n, table[i].nb,
+              table[i].gflops, i + 1 < table.size() ? "," : "");
+    fprintf(f, "  ]\n}\n");
+    fclose(f);
+  }
+  return 0;
+}
+
+int lu_load_table(const char* path) {
+  if (!path) return -1;
+  FILE* f = fopen(path, "r");
+  if (!f) return -1;
+  std::string s;
+  char buf[4096];
+  size_t r;
+  while ((r = fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, r);
+  fclose(f);
+  std::vector<LEntry> t;
+  size_t p = s.find("\"entries\"");
+  if (p == std::string::npos) return -1;
+  while ((p = s.find("{\"n\":", p)) != std::string::npos) {
+    LEntry e;
+    long long n;
+    if (sscanf(s.c_str() + p, "{\"n\": %lld, \"nb\": %d, \"gflops\": %lf", &n, &e.nb, &e.gflops) != 3) return -1;
+    if (!lu_nb_ok(e.nb)) return -1;
+    e.n = n;
+    t.push_back(e);
+    ++p;
+  }
+  std::lock_guard<std::mutex> lock(g_ltmu);
+  g_ltab = t;
+  return 0;
+}
+
+int lu_lookup(int64_t n, int* nb) {
+  if (n < 0) return -1;
+  if (!nb) return -2;
+  lu_table_lookup(n, nb);
+  return 0;
+}
+
+int lu_clear_table(void) {
+  std::lock_guard<std::mutex> lock(g_ltmu);
+  g_ltab.clear();
+  return 0;
+}
+
 }  // extern "C"
+
+int lu_table_lookup(int64_t n, int* nb) {
+  std::lock_guard<std::mutex> lock(g_ltmu);
+  if (g_ltab.empty()) {
+    *nb = LMAX;  // built-in default when nothing is tuned
+    return 1;
+  }
+  const LEntry* best = &g_ltab[0];
+  for (const LEntry& e : g_ltab) {
+    const int64_t d = std::llabs(e.n - n), db = std::llabs(best->n - n);
+    if (d < db || (d == db && e.n < best->n)) best = &e;
+  }
+  *nb = best->nb;
+  return 0;
+}

@@ -117,3 +117,35 @@ def test_lu_bench_size_solve(q):
     x = lu.lu_solve(Fg, pr, nb, b)
     r = A @ x - b
     assert np.linalg.norm(r) / (np.linalg.norm(A, 2) * np.linalg.norm(x)) <= 100 * n * U
+
+
+def test_lu_tuner_matches_oracle_replay(q, tmp_path):
+    """lu_tune (Step 1 over NB 16..64, Heuristic 2, Step 2 with
+    prune-as-you-go) replayed by the oracle's restatement of the rules from
+    its own log."""
+    import ctypes
+    import json
+    import os
+
+    from oracle import tuning
+    table, log = str(tmp_path / "lt.json"), str(tmp_path / "ll.jsonl")
+    try:
+        res = q.lu_tune([256, 512, 768], heuristic=2, reps=2, table=table, log=log)
+        with open(log) as f:
+            entries = [json.loads(line) for line in f if line.strip()]
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        perf1 = {(e["nb"], 1): 2.0 * sms * 2.0 * e["nb"] ** 3 / e["seconds"] / 1e9 for e in entries if e["kind"] == 21}
+        assert sorted(perf1) == [(nb, 1) for nb in range(16, 65, 8)]
+        pre = tuning.preselect(perf1, heuristic=2)
+        step2 = {(e["n"], e["nb"]): 2.0 * e["n"] ** 3 / 3.0 / e["seconds"] for e in entries if e["kind"] == 22}
+        want, count = tuning.step2_payg([256, 512, 768], pre, lambda n, pr: step2[(n, pr[0])])
+        assert count == len(step2) == res["factorizations_timed"]
+        tab = json.load(open(table))
+        assert {e["n"]: e["nb"] for e in tab["entries"]} == {n: v[0][0] for n, v in want.items()}
+        out = ctypes.c_int()
+        assert q.lib().lu_lookup(600, ctypes.byref(out)) == 0 and out.value == want[512][0][0]
+    finally:
+        q.lib().lu_clear_table()
+        path = os.path.join(q._TUNED_DIR, "gb300_lu_fp64.json")
+        if os.path.exists(path):
+            q.lib().lu_load_table(path.encode())

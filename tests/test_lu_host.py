@@ -2,6 +2,7 @@
 its DAG against a brute-force enumeration of the tasks, workspace sizes and
 argument checks."""
 import ctypes
+import os
 
 import pytest
 
@@ -51,3 +52,29 @@ def test_workspace_and_arguments(L):
     assert L.lu_factor_d(10, P, 10, 8, P, P, 16, None) == -7                 # scratch too small
     assert L.lu_factor_d(0, Z, 1, 64, None, None, 0, None) == 0              # empty: nothing to do
     assert L.lu_status(None, ctypes.byref(ctypes.c_int()), None, None) == -1
+
+
+def test_table_lookup(L, tmp_path):
+    p = tmp_path / "lu.json"
+    p.write_text('{\n  "factorization": "lu",\n  "entries": [\n'
+                 '    {"n": 1000, "nb": 32, "gflops": 1.0},\n'
+                 '    {"n": 2000, "nb": 48, "gflops": 1.0},\n'
+                 '    {"n": 6000, "nb": 64, "gflops": 1.0}\n  ]\n}\n')
+    try:
+        assert L.lu_load_table(str(p).encode()) == 0
+        nb = ctypes.c_int()
+        for n, want in [(10, 32), (1500, 32), (1501, 48), (4000, 48), (4001, 64), (10 ** 6, 64)]:
+            assert L.lu_lookup(n, ctypes.byref(nb)) == 0
+            assert nb.value == want, (n, nb.value)
+        pe, sb = ctypes.c_int64(), ctypes.c_int64()
+        assert L.lu_workspace(1000, 0, ctypes.byref(pe), ctypes.byref(sb)) == 0 and pe.value == 32 * 32 * 32
+        bad = tmp_path / "bad.json"
+        bad.write_text('{"entries": [\n    {"n": 1000, "nb": 128, "gflops": 1.0}\n]}\n')
+        assert L.lu_load_table(str(bad).encode()) == -1  # nb outside 8..64
+    finally:
+        L.lu_clear_table()
+        nb = ctypes.c_int()
+        assert L.lu_lookup(5000, ctypes.byref(nb)) == 0 and nb.value == 64  # built-in default
+        path = os.path.join(os.path.dirname(lib_mod.__file__), "tuned", "gb300_lu_fp64.json")
+        if os.path.exists(path):
+            assert L.lu_load_table(path.encode()) == 0
