@@ -8,6 +8,8 @@
 * One tile is LU with partial pivoting: U equals LAPACK's (scipy) U.
 * Solutions agree with LAPACK's solve within the conditioning bound; a zero
   column is reported by info; planted mistakes fail the pins.
+* A column diagonally dominant matrix needs no swap anywhere, and the tile
+  factors equal the textbook unpivoted right-looking LU bit for bit.
 """
 import os
 import types
@@ -141,3 +143,29 @@ def test_mutants_fail_a_pin(old, new):
     F0, _, _ = lu.getrf_incpiv(A, 7)
     failed |= not np.allclose(F, F0)
     assert failed
+
+
+@pytest.mark.parametrize("n,nb", [(30, 7), (64, 16), (50, 50)])
+def test_diagonally_dominant_is_unpivoted_lu(n, nb):
+    """A strictly column diagonally dominant matrix keeps that property in
+    every Schur complement, so no step swaps (GETRF keeps row c, TSTRF keeps
+    U's row) and each entry sees the same subtractions in the same order as
+    in the textbook right-looking LU without pivoting: the factors agree
+    bit for bit."""
+    rng = np.random.default_rng(n + nb)
+    A = rng.uniform(-1.0, 1.0, (n, n))
+    A[np.arange(n), np.arange(n)] = np.abs(A).sum(axis=0) + 1.0
+    F, piv, info = lu.getrf_incpiv(A, nb)
+    assert info == 0
+    NT = (n + nb - 1) // nb
+    for k in range(NT):
+        nk = min(nb, n - k * nb)
+        assert all(piv[k, k, c] == c for c in range(nk))
+        assert all((piv[i, k, :nk] == -1).all() for i in range(k + 1, NT))
+    D = A.copy()
+    for c in range(n):
+        D[c + 1:, c] = D[c + 1:, c] / D[c, c]
+        for r in range(c + 1, n):
+            for j in range(c + 1, n):
+                D[r, j] = D[r, j] - D[r, c] * D[c, j]
+    assert np.array_equal(F, D)
