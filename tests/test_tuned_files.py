@@ -76,3 +76,61 @@ def test_reliability_reproduces(tmp_path, rel, log, table, run):
         assert got[k] == pytest.approx(want[k], rel=1e-12), k
     # every ratio is a grid point's time over the grid best's, from the exhaustive logs
     assert all(0 < r["ratio"] <= 1 for r in got["per_shape"])
+
+
+def test_committed_tables_load_and_answer_their_entries():
+    """Every committed table is read by the library's own readers, and a
+    lookup at each tuned shape returns that shape's entry."""
+    import ctypes
+
+    from paper_1102_5328_gb300 import _lib
+    L = _lib.load()
+    j = lambda n: os.path.join(TUNED, n)
+    try:
+        for name, prec in (("gb300_fp64.json", 0), ("gb300_fp32.json", 1)):
+            L.qr_clear_tables()
+            assert L.qr_load_table(j(name).encode()) == 0, name
+            nb, ib, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            for e in _table(name)["entries"]:
+                assert L.qr_lookup_p(e["m"], e["n"], prec, ctypes.byref(nb), ctypes.byref(ib), ctypes.byref(p)) == 0
+                assert (nb.value, ib.value, p.value) == (e["nb"], e["ib"], e.get("p", 1)), (name, e)
+        for name, load, look in (("gb300_chol_fp64.json", L.chol_load_table, L.chol_lookup),
+                                 ("gb300_lu_fp64.json", L.lu_load_table, L.lu_lookup)):
+            assert load(j(name).encode()) == 0, name
+            v = ctypes.c_int()
+            for e in _table(name)["entries"]:
+                assert look(e["n"], ctypes.byref(v)) == 0 and v.value == e["nb"], (name, e)
+    finally:
+        L.qr_clear_tables()
+        for name in ("gb300_fp64.json", "gb300_fp32.json"):
+            L.qr_load_table(j(name).encode())
+
+
+def test_write_table_round_trips(tmp_path):
+    """tune.write_table writes the one-entry-per-line layout the C reader
+    takes (the merged SM-budget tables go through it)."""
+    import ctypes
+
+    from paper_1102_5328_gb300 import _lib
+    torch = pytest.importorskip("torch")  # tune imports torch
+    from paper_1102_5328_gb300 import tune
+    L = _lib.load()
+    tab = {"prec": "fp64", "heuristic": 2, "entries": [
+        {"m": 1000, "n": 1000, "nb": 64, "ib": 16, "p": 1, "gflops": 68.1, "sms": 0},
+        {"m": 20000, "n": 500, "nb": 64, "ib": 16, "p": 32, "gflops": 311.3, "sms": 0},
+        {"m": 1000, "n": 1000, "nb": 128, "ib": 8, "p": 1, "gflops": 50.0, "sms": 19}]}
+    path = str(tmp_path / "w.json")
+    tune.write_table(path, tab)
+    assert json.load(open(path)) == tab
+    try:
+        L.qr_clear_tables()
+        assert L.qr_load_table(path.encode()) == 0
+        nb, ib, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        assert L.qr_lookup_sms(1000, 1000, 0, 19, ctypes.byref(nb), ctypes.byref(ib), ctypes.byref(p)) == 0
+        assert (nb.value, ib.value, p.value) == (128, 8, 1)
+        assert L.qr_lookup_p(22000, 480, 0, ctypes.byref(nb), ctypes.byref(ib), ctypes.byref(p)) == 0
+        assert (nb.value, ib.value, p.value) == (64, 16, 32)
+    finally:
+        L.qr_clear_tables()
+        for name in ("gb300_fp64.json", "gb300_fp32.json"):
+            L.qr_load_table(os.path.join(TUNED, name).encode())
