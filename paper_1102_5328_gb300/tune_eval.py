@@ -53,19 +53,34 @@ def nearest_shape(shape, tuned):
     return min(tuned, key=lambda t: (abs(t[0] - m) + abs(t[1] - n), t[0] + t[1]))
 
 
-def replay(heuristic, step1, es, tuned_shapes, sms=152):
+def widen(perf, sel, tol):
+    """QR_OPT_TUNE_IB_TOL as qr_tune applies it: each preselected (NB, IB*)
+    also brings the IBs of that NB whose Step-1 rate is at least (1 - tol)
+    times IB*'s, ascending IB after IB*."""
+    out = []
+    for nb, ib0 in sel:
+        out.append((nb, ib0))
+        if tol > 0:
+            out += [(n2, ib) for (n2, ib) in sorted(perf) if n2 == nb and ib != ib0 and perf[(n2, ib)] >= (1.0 - tol) * perf[(nb, ib0)]]
+    return out
+
+
+def replay(heuristic, step1, es, tuned_shapes, sms=152, ib_tol=0.0):
     """Run the PS(+PAYG) decision procedure on logged timings with the
-    library's rule functions. Returns ({shape: pair}, step2_seconds)."""
+    library's rule functions (and the IB tolerance ib_tol). Returns
+    ({shape: pair}, step2_seconds, pairs preselected)."""
     L = lib()
     pairs = sorted(step1)
     k = len(pairs)
     nb = (ctypes.c_int * k)(*[p[0] for p in pairs])
     ib = (ctypes.c_int * k)(*[p[1] for p in pairs])
-    perf = (ctypes.c_double * k)(*[2 * sms * 4.0 * p[0] ** 3 / step1[p] / 1e9 for p in pairs])
+    pf = {p: 2 * sms * 4.0 * p[0] ** 3 / step1[p] / 1e9 for p in pairs}
+    perf = (ctypes.c_double * k)(*[pf[p] for p in pairs])
     snb = (ctypes.c_int * 64)()
     sib = (ctypes.c_int * 64)()
     ns = L.qr_tune_preselect(k, nb, ib, perf, heuristic, 8, 8, snb, sib)
-    surv = [(snb[i], sib[i]) for i in range(ns)]
+    surv = widen(pf, [(snb[i], sib[i]) for i in range(ns)], ib_tol)
+    ns = len(surv)
     table, cost = {}, 0.0
     for shape in sorted(tuned_shapes, key=lambda s: (s[1], s[0])):
         m, n = shape
@@ -95,6 +110,8 @@ def main(argv=None):
     ap.add_argument("--es-json", default="", help="JSON line printed by the exhaustive run")
     ap.add_argument("--tuned", default="1000,2000,4000,6000,8000,10000")
     ap.add_argument("--heldout", default="2700,4200,5000")
+    ap.add_argument("--ib-tols", default="",
+                    help="also replay Heuristic 2 with these IB tolerances (per mille, comma-separated)")
     ap.add_argument("--out", default="")
     a = ap.parse_args(argv)
 
@@ -166,6 +183,17 @@ def main(argv=None):
         reps["H%d" % h] = {"preselected": nsel, "step2_seconds_6runs": cost, "mean_ratio": float(np.mean(rr)),
                            "min_ratio": float(np.min(rr))}
     res["replayed_heuristics"] = reps
+    if a.ib_tols:
+        sweep = {}
+        for tol in [int(v) for v in a.ib_tols.split(",") if v]:
+            t, cost, nsel = replay(2, step1, es, tuned, ib_tol=tol / 1000.0)
+            rr = []
+            for shape in tuned + held:
+                best, pbest, cands = es_best(shape)
+                rr.append(cands[t[nearest_shape(shape, list(t))]] / pbest)
+            sweep[str(tol)] = {"preselected": nsel, "step2_seconds_6runs": cost, "mean_ratio": float(np.mean(rr)),
+                               "min_ratio": float(np.min(rr))}
+        res["replayed_ib_tolerance_permille"] = sweep
     s = json.dumps(res, indent=1)
     if a.out:
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)

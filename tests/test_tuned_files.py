@@ -134,3 +134,37 @@ def test_write_table_round_trips(tmp_path):
         L.qr_clear_tables()
         for name in ("gb300_fp64.json", "gb300_fp32.json"):
             L.qr_load_table(os.path.join(TUNED, name).encode())
+
+
+def test_tune_eval_widening_is_the_oracles():
+    """tune_eval's replay of the IB tolerance applies the oracle's rule
+    (random Step-1 tables, several tolerances)."""
+    import random
+
+    from paper_1102_5328_gb300 import tune_eval
+    rng = random.Random(5)
+    for _ in range(50):
+        perf = {(nb, ib): rng.uniform(100, 200) for nb in (64, 96, 128) for ib in (8, 16, 32)}
+        pre = tuning.preselect(perf, heuristic=2)
+        for tol in (0.0, 0.01, 0.05, 0.2):
+            assert tune_eval.widen(perf, pre, tol) == tuning.widen_ib(perf, pre, tol)
+
+
+def test_ib_tolerance_sweep_reproduces():
+    from paper_1102_5328_gb300 import tune_eval
+    import io
+    import contextlib
+    j = lambda n: os.path.join(TUNED, n)
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        assert tune_eval.main(["--es", j("gb300_fp64_es.jsonl"), "--es-held", j("gb300_fp64_es_held.jsonl"),
+                               "--pspayg", j("gb300_fp64_h2.jsonl"), "--table", j("gb300_fp64_h2.json"),
+                               "--ib-tols", "0,5,10,15,20,30,50,100"]) == 0
+    got = json.loads(buf.getvalue())["replayed_ib_tolerance_permille"]
+    want = _table("gb300_fp64_ib_tol_sweep.json")["replayed_ib_tolerance_permille"]
+    assert got.keys() == want.keys()
+    for k in want:
+        for f in ("preselected", "step2_seconds_6runs", "mean_ratio", "min_ratio"):
+            assert got[k][f] == pytest.approx(want[k][f], rel=1e-12), (k, f)
+    # tolerance 0 is the paper's Heuristic 2
+    assert want["0"]["mean_ratio"] == pytest.approx(_table("gb300_fp64_h2_reliability.json")["replayed_heuristics"]["H2"]["mean_ratio"])
