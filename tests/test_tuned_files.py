@@ -168,3 +168,51 @@ def test_ib_tolerance_sweep_reproduces():
             assert got[k][f] == pytest.approx(want[k][f], rel=1e-12), (k, f)
     # tolerance 0 is the paper's Heuristic 2
     assert want["0"]["mean_ratio"] == pytest.approx(_table("gb300_fp64_h2_reliability.json")["replayed_heuristics"]["H2"]["mean_ratio"])
+
+
+def test_installed_table_replays_as_a_model_guided_search():
+    """The installed table's own log (Step 1, every Step-2 timing, the
+    model's logged predictions, kind 4) replayed by the rules: Step 1 ->
+    Heuristic 2 widened by the 2 % IB tolerance; at each shape, ascending
+    n, the pairs timed are the model's k = 1 best, extended down its ranking
+    while the last one timed was the fastest so far, and all survivors when
+    a timed pair's measured / predicted ratio differs from the top-ranked
+    one's by more than e^0.25; shapes without predictions are timed in full;
+    prune-as-you-go between square orders. The logged timings are exactly
+    those pairs and the table holds each shape's fastest."""
+    import math
+    L, tab = _log("gb300_fp64_pspayg.jsonl"), _table("gb300_fp64.json")
+    perf1 = {(e["nb"], e["ib"]): 2.0 * SMS * 4.0 * e["nb"] ** 3 / e["seconds"] / 1e9 for e in L if e["kind"] == 1}
+    surv = tuning.widen_ib(perf1, tuning.preselect(perf1, heuristic=2), 0.02)
+    sec2 = {(e["m"], e["n"], e["nb"], e["ib"]): e["seconds"] for e in L if e["kind"] == 2}
+    pred = {(e["m"], e["n"], e["nb"], e["ib"]): e["seconds"] for e in L if e["kind"] == 4}
+    shapes = sorted({(e["m"], e["n"]) for e in L if e["kind"] == 2}, key=lambda s: (s[1], s[0]))
+    k, guided = 1, 0
+    timed_log = {}
+    for e in L:
+        if e["kind"] == 2:
+            timed_log.setdefault((e["m"], e["n"]), set()).add((e["nb"], e["ib"]))
+    entries = {(e["m"], e["n"]): (e["nb"], e["ib"]) for e in tab["entries"]}
+    for m, n in shapes:
+        if any((m, n) + pr in pred for pr in surv):
+            guided += 1
+            rank = sorted(range(len(surv)), key=lambda c: pred[(m, n) + surv[c]])
+            timed = [rank[0]]
+            r = 1
+            while r < len(surv) and min(timed, key=lambda c: (sec2[(m, n) + surv[c]], timed.index(c))) == timed[-1]:
+                timed.append(rank[r])
+                r += 1
+            scale = math.log(sec2[(m, n) + surv[timed[0]]]) - math.log(pred[(m, n) + surv[timed[0]]])
+            if any(abs(math.log(sec2[(m, n) + surv[c]]) - math.log(pred[(m, n) + surv[c]]) - scale) > 0.25
+                   for c in timed[1:]):
+                timed += rank[r:]
+        else:
+            timed = list(range(len(surv)))
+        pairs = [surv[c] for c in timed]
+        assert set(pairs) == timed_log[(m, n)], (m, n)
+        perf = {pr: _flops(m, n) / sec2[(m, n) + pr] for pr in pairs}
+        assert entries[(m, n)] == max(pairs, key=lambda pr: (perf[pr], -pr[0])), (m, n)
+        if m == n:
+            keep = tuning.payg_prune(pairs, perf)
+            surv = [pr for pr in surv if pr not in pairs or pr in keep]
+    assert guided >= 3  # the third square order on
